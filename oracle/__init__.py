@@ -1,0 +1,28 @@
+"""CPU oracle for the tournament-pivoting LU hot path (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``lu_oracle.c`` (plain FP64
+C, built with gcc) through ctypes and shares nothing with the GPU library.
+
+Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
+
+* ``lu_factor``      -- pinned: GEPP special cases against LAPACK getrf,
+  closed-form L*U products, permutation and triangular matrices, cofactor
+  determinants, invariants, loop-bound counts of Section 6, and an independent
+  exact-rational tournament on tiny inputs.
+* ``tslu_select``    -- pinned through the same tests (b = 1 and one-leaf
+  cases reduce to partial pivoting; brute force on tiny inputs).
+* ``lu_solve``       -- pinned against numpy.linalg.solve and exact integer
+  systems.
+* ``backward_error`` -- pinned against closed forms (exact solutions give 0,
+  hand-computed small cases).
+"""
+from .oracle import (  # noqa: F401
+    build,
+    lib_path,
+    lu_factor,
+    lu_solve,
+    tslu_select,
+    backward_error,
+    set_threads,
+)

@@ -1,0 +1,135 @@
+"""ctypes binding of the plain-C FP64 oracle (test infrastructure only).
+
+Every function takes and returns numpy arrays; matrices are row-major
+float64, the layout the GPU library also uses.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import platform
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lu_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "_build", f"liblu_oracle_{platform.machine()}.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile lu_oracle.c with gcc (-ffp-contract=off keeps every fused
+    operation explicit).  Returns the shared-library path."""
+    out = lib_path()
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+class _Counts(ctypes.Structure):
+    _fields_ = [("s1_div", ctypes.c_longlong), ("s2_fma", ctypes.c_longlong)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            lib.oracle_lu_factor.argtypes = [I, I, P, I, I, I, P, P, P]
+            lib.oracle_lu_factor.restype = I
+            lib.oracle_tslu_select.argtypes = [I, I, P, I, I, I, P]
+            lib.oracle_tslu_select.restype = I
+            lib.oracle_lu_solve.argtypes = [I, I, P, I, P, P, I]
+            lib.oracle_lu_solve.restype = I
+            lib.oracle_backward_error.argtypes = [I, I, P, I, P, I, P, I, P]
+            lib.oracle_backward_error.restype = None
+            lib.oracle_set_threads.argtypes = [I]
+            lib.oracle_set_threads.restype = I
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def set_threads(n: int = 0) -> int:
+    """Set the OpenMP thread count (0 = leave as is); returns the count used."""
+    return _load().oracle_set_threads(int(n))
+
+
+def lu_factor(A: np.ndarray, b: int, h: int = 128, count: bool = False):
+    """Tournament-pivoting LU of an m x n matrix.
+
+    Returns (LU, piv, info) or (LU, piv, info, (s1_div, s2_fma)) when
+    ``count``; LU is a new array, piv is 0-based LAPACK-style (int32)."""
+    lib = _load()
+    LU = np.ascontiguousarray(A, dtype=np.float64).copy()
+    m, n = LU.shape
+    piv = np.zeros(max(min(m, n), 1), dtype=np.int32)
+    info = ctypes.c_int(0)
+    cnt = _Counts()
+    rc = lib.oracle_lu_factor(m, n, _ptr(LU), max(n, 1), int(b), int(h), _ptr(piv),
+                              ctypes.byref(info), ctypes.byref(cnt))
+    if rc != 0:
+        raise ValueError(f"oracle_lu_factor: argument {-rc} invalid")
+    piv = piv[: min(m, n)]
+    if count:
+        return LU, piv, info.value, (cnt.s1_div, cnt.s2_fma)
+    return LU, piv, info.value
+
+
+def tslu_select(A: np.ndarray, k: int, w: int, h: int) -> np.ndarray:
+    """Winners (row positions, root pivot order) of one TournPivot on panel
+    columns [k, k+w) over active rows [k, m) of A's current values."""
+    lib = _load()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    m, n = A.shape
+    win = np.zeros(w, dtype=np.int32)
+    rc = lib.oracle_tslu_select(m, max(n, 1), _ptr(A), int(k), int(w), int(h), _ptr(win))
+    if rc != 0:
+        raise ValueError("oracle_tslu_select: bad arguments")
+    return win
+
+
+def lu_solve(LU: np.ndarray, piv: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """X = U^{-1} L^{-1} P B for the oracle's factors; B is n or n x nrhs."""
+    lib = _load()
+    LU = np.ascontiguousarray(LU, dtype=np.float64)
+    n = LU.shape[0]
+    vec = B.ndim == 1
+    X = np.ascontiguousarray(B.reshape(n, -1), dtype=np.float64).copy()
+    nrhs = X.shape[1]
+    piv = np.ascontiguousarray(piv, dtype=np.int32)
+    rc = lib.oracle_lu_solve(n, nrhs, _ptr(LU), max(n, 1), _ptr(piv), _ptr(X), max(nrhs, 1))
+    if rc != 0:
+        raise ValueError(f"oracle_lu_solve: argument {-rc} invalid")
+    return X[:, 0] if vec else X
+
+
+def backward_error(A: np.ndarray, B: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """Per-column normwise backward error ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)."""
+    lib = _load()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    Bm = np.ascontiguousarray(B.reshape(n, -1), dtype=np.float64)
+    Xm = np.ascontiguousarray(X.reshape(n, -1), dtype=np.float64)
+    nrhs = Bm.shape[1]
+    eta = np.zeros(nrhs, dtype=np.float64)
+    lib.oracle_backward_error(n, nrhs, _ptr(A), max(n, 1), _ptr(Bm), max(nrhs, 1),
+                              _ptr(Xm), max(nrhs, 1), _ptr(eta))
+    return eta
