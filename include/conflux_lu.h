@@ -1,0 +1,116 @@
+/*
+ * conflux_lu.h -- C ABI of the GB300 tournament-pivoting LU library.
+ *
+ * The operations follow the paper's statement of the problem: in-place
+ * PA = LU of a dense matrix (Fig. 1; Algorithm 1, where A_t shrinks by v
+ * columns and the chosen rows each step), computed as a blocked right-looking
+ * LU whose v pivot rows per step come from tournament pivoting (Section 7.3)
+ * and whose block updates are the triangular solves FactorizeA10 /
+ * FactorizeA01 and the Schur update FactorizeA11 (Section 7.2).  Everything
+ * else follows LAPACK getrf/getrs conventions.
+ *
+ * Layout.  Matrices are ROW-MAJOR: element (i, j) of A sits at A[i*lda + j],
+ * lda >= max(1, columns).  Row swaps are then contiguous copies, and this is
+ * PyTorch's native layout.
+ *
+ * Ownership.  Matrix, vector, pivot and info pointers are DEVICE pointers
+ * owned by the caller, unless an argument says "host".  The library keeps no
+ * pointer past the work it enqueues on the given stream.  Internal workspace
+ * is taken from the stream-ordered allocator (cudaMallocAsync) and returned
+ * on the same stream.
+ *
+ * Asynchrony.  Every call validates its arguments on the host, enqueues its
+ * work on `stream` and returns; results are ready when the stream reaches
+ * that point.  Calls on one stream are ordered; calls that share buffers on
+ * different streams must be ordered by the caller.
+ *
+ * Status.  The return value is
+ *     0                       enqueued,
+ *    -i  (i >= 1)             argument i is invalid (checked before any work),
+ *     LU_E* (positive)        a runtime failure (see below).
+ * Numerical status goes to a caller-provided DEVICE int `info`:
+ *     0       success,
+ *     j + 1   U(j, j) is exactly zero for the first such j.  The factorization
+ *             still completes (as getrf); the L column below a zero pivot is
+ *             set to zero instead of dividing by zero.
+ * Inputs are assumed finite; results on NaN/Inf inputs are unspecified.
+ */
+#ifndef CONFLUX_LU_H
+#define CONFLUX_LU_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Runtime failure codes (positive return values). */
+#define LU_ENOMEM       1   /* workspace allocation failed                    */
+#define LU_ELAUNCH      2   /* a kernel launch or CUDA call failed            */
+#define LU_ETIMEOUT     3   /* a bounded device-side wait ran out             */
+#define LU_EBUSY        4   /* serving: no slot or HBM budget left            */
+#define LU_EUNSUPPORTED 5   /* valid but unsupported combination of options   */
+#define LU_ENOTFOUND    6   /* serving: unknown ticket                        */
+
+/* Arithmetic of the factorization. */
+typedef enum {
+    LU_PREC_F64 = 0,        /* every step in binary64                          */
+    LU_PREC_F32 = 1,        /* every step in binary32                          */
+    LU_PREC_BF16 = 2,       /* binary32 panel and solves; Schur update with
+                               bfloat16 operands, fp32 accumulation            */
+    LU_PREC_FP8 = 3         /* as BF16 but fp8 e4m3 operands with one
+                               power-of-two scale per 256 x 256 tile           */
+} lu_precision;
+
+/* Options of the blocked factorization.  Zero fields take defaults. */
+typedef struct {
+    int b;                  /* panel width v (Section 7.2 "Blocking parameter
+                               v"); default 256 for n >= 4096, else 32        */
+    int h;                  /* tournament leaf height: rows per leaf of the
+                               first round (Section 7.3); default 128          */
+    int precision;          /* lu_precision; default LU_PREC_F64               */
+    int reserved[5];        /* must be zero                                     */
+} lu_opts;
+
+/*
+ * lu_factor -- in-place PA = LU of an n x n matrix (Algorithm 1).
+ *   n      order, n >= 0
+ *   A      device, n x n row-major, lda >= max(1, n); overwritten by L (unit
+ *          lower, diagonal not stored) and U
+ *   lda    leading dimension (elements)
+ *   piv    device int[n]; piv[i] = the 0-based row that was swapped with row
+ *          i at step i (LAPACK ipiv, 0-based)
+ *   info   device int; see "Status"
+ *   stream CUDA stream (0 = legacy default stream)
+ * Uses b = 256 (n >= 4096) or 32, h = 128, binary64 throughout.
+ */
+int lu_factor(int n, double *A, int lda, int *piv, int *info, cudaStream_t stream);
+
+/*
+ * lu_factor_ex -- rectangular m x n factorization with options.  min(m, n)
+ * pivots are produced; for m < n the result is L (m x m) and an upper
+ * trapezoidal U (m x n).  opts may be NULL (defaults).  Only LU_PREC_F64 is
+ * accepted here; the mixed-precision factorization lives in lu_factor_mixed.
+ * Tournament nodes hold up to max(leaf rows, 2b) x b panel values in the
+ * shared memory of one thread-block cluster: b <= 256 and
+ * max(h', 2b) * b <= 204800 where h' is the first tree level's row count.
+ */
+int lu_factor_ex(int m, int n, double *A, int lda, int *piv, int *info,
+                 const lu_opts *opts, cudaStream_t stream);
+
+/*
+ * lu_solve -- X = U^{-1} L^{-1} P B with the factors of lu_factor.
+ *   n, LU, lda, piv  as returned by lu_factor (device)
+ *   nrhs  number of right-hand sides, nrhs >= 0
+ *   B     device, n x nrhs row-major, ldb >= max(1, nrhs); overwritten by X
+ */
+int lu_solve(int n, int nrhs, const double *LU, int lda, const int *piv,
+             double *B, int ldb, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CONFLUX_LU_H */

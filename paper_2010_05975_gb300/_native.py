@@ -1,0 +1,93 @@
+"""ctypes loader for the in-tree CUDA library (no fallback of any kind)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+LU_ENOMEM = 1
+LU_ELAUNCH = 2
+LU_ETIMEOUT = 3
+LU_EBUSY = 4
+LU_EUNSUPPORTED = 5
+LU_ENOTFOUND = 6
+
+LU_PREC_F64 = 0
+LU_PREC_F32 = 1
+LU_PREC_BF16 = 2
+LU_PREC_FP8 = 3
+
+_NAMES = {LU_ENOMEM: "LU_ENOMEM", LU_ELAUNCH: "LU_ELAUNCH", LU_ETIMEOUT: "LU_ETIMEOUT",
+          LU_EBUSY: "LU_EBUSY", LU_EUNSUPPORTED: "LU_EUNSUPPORTED", LU_ENOTFOUND: "LU_ENOTFOUND"}
+
+
+class LuError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        self.code = code
+        what = f"argument {-code} invalid" if code < 0 else _NAMES.get(code, f"error {code}")
+        super().__init__(f"{fn}: {what}")
+
+
+class lu_opts(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_int), ("h", ctypes.c_int), ("precision", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+P = ctypes.c_void_p
+I = ctypes.c_int
+
+# name -> (argtypes, restype)
+_SIGS = {
+    "lu_factor": ([I, P, I, P, P, P], I),
+    "lu_factor_ex": ([I, I, P, I, P, P, ctypes.POINTER(lu_opts), P], I),
+    "lu_solve": ([I, I, P, I, P, P, I, P], I),
+}
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def library(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load the shared library.  Raises if it was not built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path) or not _build.up_to_date():
+                if not build_if_missing:
+                    raise RuntimeError(
+                        f"CUDA library {path} is missing or stale; build it with "
+                        "paper_2010_05975_gb300.build.build() (nvcc, sm_103a)")
+                _build.build()
+            lib = ctypes.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(lib, name, None)
+                if fn is None:
+                    continue
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def register(name: str, argtypes, restype=ctypes.c_int):
+    _SIGS[name] = (argtypes, restype)
+    if _lib is not None and hasattr(_lib, name):
+        fn = getattr(_lib, name)
+        fn.argtypes = argtypes
+        fn.restype = restype
+
+
+def exported_symbols(lib: ctypes.CDLL, names) -> dict:
+    return {n: hasattr(lib, n) for n in names}
+
+
+def check(fn: str, rc: int) -> None:
+    if rc != 0:
+        raise LuError(fn, rc)

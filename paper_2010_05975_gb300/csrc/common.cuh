@@ -1,0 +1,62 @@
+// Internal helpers shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include "../../include/conflux_lu.h"
+
+#define LU_TRY(expr)                                                  \
+    do {                                                              \
+        cudaError_t e_ = (expr);                                      \
+        if (e_ != cudaSuccess) return LU_ELAUNCH;                     \
+    } while (0)
+
+#define LU_LAUNCHED()                                                 \
+    do {                                                              \
+        if (cudaPeekAtLastError() != cudaSuccess) {                   \
+            cudaGetLastError();                                       \
+            return LU_ELAUNCH;                                        \
+        }                                                             \
+    } while (0)
+
+namespace lu {
+
+constexpr int kMaxPanel = 256;          // largest supported panel width b
+constexpr int kTsluThreads = 256;       // threads per tournament CTA
+constexpr int kTsluMaxCluster = 8;      // portable cluster size
+
+__host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ inline size_t idx(int i, int j, int ld) {
+    return static_cast<size_t>(i) * static_cast<size_t>(ld) + static_cast<size_t>(j);
+}
+
+// Tournament geometry of one step: rows [k, m), panel [k, k+w).
+struct TsluShape {
+    int H;        // rows of a first-level node (a "super-leaf")
+    int nsuper;   // number of first-level nodes
+    int nr_max;   // most rows any node stacks
+    int C;        // CTAs per node (cluster size)
+    int R;        // rows per CTA
+    size_t smem;  // dynamic shared memory per CTA (bytes)
+};
+
+// Leaves of h rows whose selection keeps every row (h <= w) are merged
+// upward until a node holds more than w rows: selection is independent of
+// the order in which candidate rows are stacked, so a node made only of
+// such leaves selects from its whole contiguous row range.
+TsluShape tslu_shape(int m, int k, int w, int h);
+
+// Host entry points of the FP64 pieces (stream-ordered, no sync).
+int tslu_select_f64(const double* A, int lda, int m, int k, int w, int h,
+                    int* lists, int* counts, size_t list_stride_nodes,
+                    double* a00, int* info, const int** root_list, cudaStream_t s);
+int pivot_apply_f64(double* A, int lda, int m, int n, int k, int w,
+                    const int* root_list, const double* a00, int* piv,
+                    int* mv, cudaStream_t s);
+int trsm_l21_f64(double* A, int lda, int m, int k, int w, cudaStream_t s);
+int trsm_u12_f64(double* A, int lda, int n, int k, int w, cudaStream_t s);
+int schur_f64(double* A, int lda, int m, int n, int k, int w, cudaStream_t s);
+int getrs_f64(int n, int nrhs, const double* LU, int lda, const int* piv,
+              double* B, int ldb, cudaStream_t s);
+
+}  // namespace lu

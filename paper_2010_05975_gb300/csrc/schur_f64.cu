@@ -1,0 +1,108 @@
+// FactorizeA11 (Section 7.2) in binary64: A22 -= L21 * U12, K = w <= 256.
+//
+// GB300 executes binary64 on the CUDA cores only (no tcgen05 kind for it;
+// measured DFMA ~1.19 TFLOP/s per GPU, DMMA m8n8k4 slower), so this is a
+// register-tiled DFMA kernel: a CTA tile of BM x BN outputs, 256 threads,
+// TM x TN accumulators per thread, K staged through shared memory in
+// double-buffered chunks of 8.  Each accumulator starts from the A22 value
+// and receives fma(-l, u, acc) for p = 0, 1, ..., w-1, the oracle's order, so
+// the result is bit-identical to it.
+#include "common.cuh"
+
+namespace lu {
+
+template <int BM, int BN>
+__global__ void __launch_bounds__(256) schur_f64_kernel(double* __restrict__ A, int lda, int m, int n, int k, int w) {
+    constexpr int BK = 8;
+    constexpr int TM = BM / 16, TN = BN / 16;
+    constexpr int APT = BM * BK / 256;          // A elements loaded per thread per chunk
+    constexpr int BPT = BN * BK / 256;          // B elements loaded per thread per chunk
+    constexpr int BTPR = BN / BPT;              // threads per B row
+    __shared__ double As[2][BK][BM];
+    __shared__ double Bs[2][BK][BN];
+
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int row0 = k + w + blockIdx.y * BM;
+    const int col0 = k + w + blockIdx.x * BN;
+
+    double acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+            acc[i][j] = (r < m && c < n) ? A[idx(r, c, lda)] : 0.0;
+        }
+
+    // loader coordinates
+    const int a_r = tid % BM, a_k = (tid / BM) * APT;
+    const int b_k = tid / BTPR, b_c = (tid % BTPR) * BPT;
+    const bool a_row_ok = (row0 + a_r) < m;
+    const double* a_src = A + idx(row0 + a_r < m ? row0 + a_r : row0, k, lda);
+    const double* b_src = A + idx(k, col0 + b_c, lda);
+
+    double ra[APT], rb[BPT];
+    auto load_chunk = [&](int kc) {
+#pragma unroll
+        for (int e = 0; e < APT; ++e) {
+            const int kk = kc + a_k + e;
+            ra[e] = (a_row_ok && kk < w) ? a_src[kk] : 0.0;
+        }
+        const int kk = kc + b_k;
+#pragma unroll
+        for (int e = 0; e < BPT; ++e) {
+            const int c = col0 + b_c + e;
+            rb[e] = (kk < w && c < n) ? b_src[idx(kc + b_k, e, lda)] : 0.0;
+        }
+    };
+    auto store_chunk = [&](int buf) {
+#pragma unroll
+        for (int e = 0; e < APT; ++e) As[buf][a_k + e][a_r] = ra[e];
+#pragma unroll
+        for (int e = 0; e < BPT; ++e) Bs[buf][b_k][b_c + e] = rb[e];
+    };
+
+    const int nchunk = cdiv(w, BK);
+    load_chunk(0);
+    store_chunk(0);
+    __syncthreads();
+    for (int ch = 0; ch < nchunk; ++ch) {
+        const int buf = ch & 1;
+        if (ch + 1 < nchunk) load_chunk((ch + 1) * BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double av[TM], bv[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) av[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bv[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(-av[i], bv[j], acc[i][j]);
+        }
+        if (ch + 1 < nchunk) store_chunk(buf ^ 1);
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+            if (r < m && c < n) A[idx(r, c, lda)] = acc[i][j];
+        }
+}
+
+int schur_f64(double* A, int lda, int m, int n, int k, int w, cudaStream_t s) {
+    const int M = m - k - w, N = n - k - w;
+    if (M <= 0 || N <= 0 || w <= 0) return 0;
+    // The DFMA pipe (about 2 FMA/clk/SM) is the bound at any tile size; 64 x 64
+    // tiles keep 88 registers per thread, two CTAs per SM and a short tail.
+    dim3 grid(cdiv(N, 64), cdiv(M, 64));
+    schur_f64_kernel<64, 64><<<grid, 256, 0, s>>>(A, lda, m, n, k, w);
+    LU_LAUNCHED();
+    return 0;
+}
+
+}  // namespace lu

@@ -1,0 +1,417 @@
+// Tournament pivoting (TournPivot, Section 7.3) and pivot application for
+// the binary64 factorization.
+//
+// One launch per tree level.  A node is handled by one thread-block cluster
+// of C CTAs; each CTA holds up to R of the node's candidate rows (their
+// current panel values) in shared memory.  A GEPP column step is
+//   local argmax  ->  one cluster barrier  ->  every CTA reads the C local
+//   winners and the pivot row through distributed shared memory  ->  local
+//   rank-1 update of its unchosen rows.
+// The arithmetic per element is the oracle's: multiplier = a / pivot (IEEE
+// division), update a = fma(-l, u, a) in ascending pivot order; ties in |a|
+// go to the smallest row position.  Because a node's choice does not depend
+// on the order its candidates are stacked in, the first tree levels, whose
+// nodes keep all their rows, are skipped: the first launched level takes
+// contiguous row ranges of H rows.
+#include "common.cuh"
+#include <cooperative_groups.h>
+#include <climits>
+
+namespace cg = cooperative_groups;
+
+namespace lu {
+
+TsluShape tslu_shape(int m, int k, int w, int h) {
+    TsluShape s{};
+    const int nact = m - k;
+    int H = h;
+    if (h <= w) {
+        H = h;
+        while (H <= w) H *= 2;
+    }
+    s.H = H;
+    s.nsuper = cdiv(nact, H);
+    s.nr_max = (s.nsuper == 1) ? nact : (H > 2 * w ? H : 2 * w);
+    int C = 1, R = s.nr_max;
+    while (C < kTsluMaxCluster && static_cast<long long>(R) * (w + 1) > 8192) {
+        C *= 2;
+        R = cdiv(s.nr_max, C);
+    }
+    s.C = C;
+    s.R = R;
+    s.smem = static_cast<size_t>(R) * (w + 1) * sizeof(double) + static_cast<size_t>(w) * sizeof(double) +
+             static_cast<size_t>(R) * 2 * sizeof(int) + static_cast<size_t>(w) * sizeof(int);
+    return s;
+}
+
+struct LevelArgs {
+    const double* A;
+    int lda, m, k, w, H;
+    int level;          // 0: first launched level (contiguous row ranges)
+    int nnode;          // nodes at this level
+    int nchild;         // nodes at the level below (level > 0)
+    int root;           // this level is the root (one node)
+    const int* child_list;
+    const int* child_cnt;
+    int* out_list;      // node-major, stride w
+    int* out_cnt;
+    double* a00;        // root: w x w rows of the factored winners, pivot order
+    int* info;          // root: first zero pivot
+    int C, R;
+};
+
+__device__ __forceinline__ bool better(double v1, int p1, double v2, int p2) {
+    return v1 > v2 || (v1 == v2 && p1 < p2);
+}
+
+__device__ __forceinline__ void warp_argmax(double& v, int& p, int& l) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        double ov = __shfl_down_sync(0xffffffffu, v, off);
+        int op = __shfl_down_sync(0xffffffffu, p, off);
+        int ol = __shfl_down_sync(0xffffffffu, l, off);
+        if (better(ov, op, v, p)) {
+            v = ov;
+            p = op;
+            l = ol;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs a) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = static_cast<int>(cluster.block_rank());
+    const int node = blockIdx.x / a.C;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarp = blockDim.x >> 5;
+    const int w = a.w, ws = w + 1;
+
+    int nr, r0 = 0, cl = 0;
+    const int* lp = nullptr;
+    const int* rp = nullptr;
+    if (a.level == 0) {
+        r0 = a.k + node * a.H;
+        nr = min(a.H, a.m - r0);
+    } else {
+        const int left = 2 * node, right = 2 * node + 1;
+        cl = a.child_cnt[left];
+        lp = a.child_list + static_cast<size_t>(left) * w;
+        if (right >= a.nchild) {            // odd last node goes up unchanged
+            if (q == 0) {
+                for (int i = tid; i < cl; i += blockDim.x) a.out_list[static_cast<size_t>(node) * w + i] = lp[i];
+                if (tid == 0) a.out_cnt[node] = cl;
+            }
+            return;
+        }
+        rp = a.child_list + static_cast<size_t>(right) * w;
+        nr = cl + a.child_cnt[right];
+    }
+    if (!(a.root || nr > w)) {              // a node that keeps all its rows
+        if (q == 0) {
+            for (int i = tid; i < nr; i += blockDim.x) a.out_list[static_cast<size_t>(node) * w + i] = r0 + i;
+            if (tid == 0) a.out_cnt[node] = nr;
+        }
+        return;
+    }
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* W = reinterpret_cast<double*>(smem_raw);    // R x ws
+    double* prow = W + static_cast<size_t>(a.R) * ws;    // w
+    int* ids = reinterpret_cast<int*>(prow + w);          // R
+    int* ord = ids + a.R;                                 // R
+    int* winp = ord + a.R;                                // w
+    __shared__ double slot_v[2];
+    __shared__ int slot_p[2], slot_l[2];
+    __shared__ double part_v[32];
+    __shared__ int part_p[32], part_l[32];
+    __shared__ int s_owner, s_lr, s_pos, s_zero;
+
+    const int i0 = q * a.R;
+    const int nloc = max(0, min(a.R, nr - i0));
+    for (int r = warp; r < nloc; r += nwarp) {
+        const int gi = i0 + r;
+        const int pos = (a.level == 0) ? (r0 + gi) : (gi < cl ? lp[gi] : rp[gi - cl]);
+        if (lane == 0) {
+            ids[r] = pos;
+            ord[r] = -1;
+        }
+        const double* src = a.A + idx(pos, a.k, a.lda);
+        for (int j = lane; j < w; j += 32) W[r * ws + j] = src[j];
+    }
+    if (tid == 0) s_zero = -1;
+    __syncthreads();
+
+    const int ns = min(nr, w);
+    for (int c = 0; c < ns; ++c) {
+        // 1. local argmax of |W[r][c]| over unchosen rows
+        double bv = -1.0;
+        int bp = INT_MAX, bl = -1;
+        for (int r = tid; r < nloc; r += blockDim.x) {
+            if (ord[r] < 0) {
+                double v = fabs(W[r * ws + c]);
+                if (!(v == v)) v = INFINITY;        // a NaN row still wins: the step always has a pivot row
+                const int p = ids[r];
+                if (better(v, p, bv, bp)) {
+                    bv = v;
+                    bp = p;
+                    bl = r;
+                }
+            }
+        }
+        warp_argmax(bv, bp, bl);
+        if (lane == 0) {
+            part_v[warp] = bv;
+            part_p[warp] = bp;
+            part_l[warp] = bl;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            bv = lane < nwarp ? part_v[lane] : -1.0;
+            bp = lane < nwarp ? part_p[lane] : INT_MAX;
+            bl = lane < nwarp ? part_l[lane] : -1;
+            warp_argmax(bv, bp, bl);
+            if (lane == 0) {
+                slot_v[c & 1] = bv;
+                slot_p[c & 1] = bp;
+                slot_l[c & 1] = bl;
+            }
+        }
+        cluster.sync();
+        // 2. cluster-wide winner, identical in every CTA
+        if (warp == 0) {
+            double v = -1.0;
+            int p = INT_MAX, l = -1;
+            if (lane < a.C) {
+                v = cluster.map_shared_rank(slot_v, lane)[c & 1];
+                p = cluster.map_shared_rank(slot_p, lane)[c & 1];
+                l = cluster.map_shared_rank(slot_l, lane)[c & 1];
+            }
+            int o = (lane < a.C) ? lane : -1;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                double ov = __shfl_down_sync(0xffffffffu, v, off);
+                int op = __shfl_down_sync(0xffffffffu, p, off);
+                int ol = __shfl_down_sync(0xffffffffu, l, off);
+                int oo = __shfl_down_sync(0xffffffffu, o, off);
+                if (better(ov, op, v, p)) {
+                    v = ov;
+                    p = op;
+                    l = ol;
+                    o = oo;
+                }
+            }
+            if (lane == 0) {
+                s_owner = o;
+                s_lr = l;
+                s_pos = p;
+            }
+        }
+        __syncthreads();
+        const int owner = s_owner, lr = s_lr;
+        // 3. pivot row from the owner's shared memory (never written again)
+        const double* rW = cluster.map_shared_rank(W, owner);
+        for (int j = c + tid; j < w; j += blockDim.x) prow[j] = rW[lr * ws + j];
+        if (tid == 0) {
+            winp[c] = s_pos;
+            if (owner == q) ord[lr] = c;
+        }
+        __syncthreads();
+        // 4. multipliers and rank-1 update of the unchosen local rows
+        const double pv = prow[c];
+        if (pv != 0.0) {
+            for (int r = warp; r < nloc; r += nwarp) {
+                if (ord[r] >= 0) continue;
+                const double l = W[r * ws + c] / pv;
+                __syncwarp();
+                if (lane == 0) W[r * ws + c] = l;
+                for (int j = c + 1 + lane; j < w; j += 32) W[r * ws + j] = fma(-l, prow[j], W[r * ws + j]);
+            }
+        } else if (tid == 0 && s_zero < 0) {
+            s_zero = c;
+        }
+        __syncthreads();
+    }
+
+    if (q == 0) {
+        for (int i = tid; i < ns; i += blockDim.x) a.out_list[static_cast<size_t>(node) * w + i] = winp[i];
+        if (tid == 0) a.out_cnt[node] = ns;
+    }
+    if (a.root) {
+        for (int r = warp; r < nloc; r += nwarp) {
+            const int o = ord[r];
+            if (o < 0) continue;
+            for (int j = lane; j < w; j += 32) a.a00[static_cast<size_t>(o) * w + j] = W[r * ws + j];
+        }
+        if (q == 0 && tid == 0 && s_zero >= 0 && *a.info == 0) *a.info = a.k + s_zero + 1;
+    }
+    cluster.sync();     // no CTA leaves while another may still read its shared memory
+}
+
+static int launch_level(const LevelArgs& args, int nnode, int C, size_t smem, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(nnode * C));
+    cfg.blockDim = dim3(kTsluThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(C);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    LU_TRY(cudaLaunchKernelEx(&cfg, tslu_level_kernel, args));
+    return 0;
+}
+
+int tslu_select_f64(const double* A, int lda, int m, int k, int w, int h, int* lists, int* counts,
+                    size_t list_stride_nodes, double* a00, int* info, const int** root_list, cudaStream_t s) {
+    const TsluShape sh = tslu_shape(m, k, w, h);
+    LU_TRY(cudaFuncSetAttribute(tslu_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(sh.smem)));
+    int* list_buf[2] = {lists, lists + list_stride_nodes * w};
+    int* cnt_buf[2] = {counts, counts + list_stride_nodes};
+    LevelArgs args{};
+    args.A = A;
+    args.lda = lda;
+    args.m = m;
+    args.k = k;
+    args.w = w;
+    args.H = sh.H;
+    args.a00 = a00;
+    args.info = info;
+    args.C = sh.C;
+    args.R = sh.R;
+
+    int nn = sh.nsuper, cur = 0;
+    args.level = 0;
+    args.nnode = nn;
+    args.nchild = 0;
+    args.root = (nn == 1);
+    args.child_list = nullptr;
+    args.child_cnt = nullptr;
+    args.out_list = list_buf[cur];
+    args.out_cnt = cnt_buf[cur];
+    if (int rc = launch_level(args, nn, sh.C, sh.smem, s)) return rc;
+    int lvl = 1;
+    while (nn > 1) {
+        const int npar = (nn + 1) / 2;
+        args.level = lvl++;
+        args.nnode = npar;
+        args.nchild = nn;
+        args.root = (npar == 1);
+        args.child_list = list_buf[cur];
+        args.child_cnt = cnt_buf[cur];
+        args.out_list = list_buf[cur ^ 1];
+        args.out_cnt = cnt_buf[cur ^ 1];
+        if (int rc = launch_level(args, npar, sh.C, sh.smem, s)) return rc;
+        cur ^= 1;
+        nn = npar;
+    }
+    *root_list = list_buf[cur];
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Pivot application.  The w winners go to rows k..k+w-1 by LAPACK-style
+// sequential swaps; one thread replays the swaps on row identities to get
+// piv[k..k+w) and the final source row of every touched position.
+// Positions touched are the top block [k, k+w) ("top t" = position k+t) and
+// the original positions of winners from below it ("slot s" = position
+// win[s] when win[s] >= k+w).  A top-origin row can be pushed into a slot
+// and be a winner later, so its location is tracked as either kind.
+// mv holds [count, dst[2w], src[2w]].
+// ---------------------------------------------------------------------------
+__global__ void pivot_moves_kernel(const int* __restrict__ win, int k, int w, int* __restrict__ piv,
+                                   int* __restrict__ mv) {
+    __shared__ int cT[kMaxPanel];   // original row now at top t
+    __shared__ int cO[kMaxPanel];   // original row now at slot s
+    __shared__ int loc[kMaxPanel];  // where the row that started at top t is: t' >= 0 top, -(s+1) slot
+    __shared__ int wn[kMaxPanel];
+    const int top = k + w;
+    for (int t = threadIdx.x; t < w; t += blockDim.x) {
+        cT[t] = k + t;
+        loc[t] = t;
+        wn[t] = win[t];
+        cO[t] = win[t];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < w; ++j) {
+            const int o = wn[j];
+            int where;                              // location of winner j
+            if (o >= top) where = -(j + 1);         // slot j is untouched before swap j
+            else where = loc[o - k];
+            const int p = (where >= 0) ? (k + where) : wn[-where - 1];
+            piv[k + j] = p;
+            if (p == k + j) continue;
+            const int ra = cT[j];
+            int rb;
+            if (where >= 0) {
+                rb = cT[where];
+                cT[where] = ra;
+            } else {
+                rb = cO[-where - 1];
+                cO[-where - 1] = ra;
+            }
+            cT[j] = rb;
+            if (ra < top) loc[ra - k] = where;
+            if (rb < top) loc[rb - k] = j;
+        }
+        int cnt = 0;
+        int* dst = mv + 1;
+        int* src = mv + 1 + 2 * w;
+        for (int t = 0; t < w; ++t)
+            if (cT[t] != k + t) {
+                dst[cnt] = k + t;
+                src[cnt] = cT[t];
+                ++cnt;
+            }
+        for (int s2 = 0; s2 < w; ++s2)
+            if (wn[s2] >= top && cO[s2] != wn[s2]) {
+                dst[cnt] = wn[s2];
+                src[cnt] = cO[s2];
+                ++cnt;
+            }
+        mv[0] = cnt;
+    }
+}
+
+// One CTA per 32-column slab: read every source row segment, then write
+// every destination, then overwrite the top block's panel columns with the
+// factored A00 taken from the tournament root.
+__global__ void __launch_bounds__(256) row_move_kernel(double* __restrict__ A, int lda, int n, int k, int w,
+                                                       const int* __restrict__ mv, const double* __restrict__ a00) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* tile = reinterpret_cast<double*>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int cnt = mv[0];
+    const int* dst = mv + 1;
+    const int* src = mv + 1 + 2 * w;
+    const int col = blockIdx.x * 32 + lane;
+    if (col < n) {
+        for (int i = warp; i < cnt; i += nwarp) tile[i * 32 + lane] = A[idx(src[i], col, lda)];
+    }
+    __syncthreads();
+    if (col < n) {
+        for (int i = warp; i < cnt; i += nwarp) A[idx(dst[i], col, lda)] = tile[i * 32 + lane];
+    }
+    __syncthreads();
+    if (col >= k && col < k + w) {
+        for (int t = warp; t < w; t += nwarp) A[idx(k + t, col, lda)] = a00[static_cast<size_t>(t) * w + (col - k)];
+    }
+}
+
+int pivot_apply_f64(double* A, int lda, int m, int n, int k, int w, const int* root_list, const double* a00,
+                    int* piv, int* mv, cudaStream_t s) {
+    (void)m;
+    pivot_moves_kernel<<<1, 256, 0, s>>>(root_list, k, w, piv, mv);
+    LU_LAUNCHED();
+    const size_t smem = static_cast<size_t>(2 * w) * 32 * sizeof(double);
+    LU_TRY(cudaFuncSetAttribute(row_move_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    row_move_kernel<<<cdiv(n, 32), 256, smem, s>>>(A, lda, n, k, w, mv, a00);
+    LU_LAUNCHED();
+    return 0;
+}
+
+}  // namespace lu
