@@ -1,0 +1,329 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 tournament-pivoting LU hot path.
+
+Default workload: one dense N = 32768 binary64 matrix, entries iid N(0, 1)
+(seed 1), panel width b = 256, tournament leaves of h = 128 rows.  A step is
+one full in-place factorization PA = LU (every row of the hot path: the
+tournament, pivot application, both triangular solves and the Schur updates)
+after the matrix is restored from a device-resident copy.  The metric is
+LU TFLOP/s = (2 N^3 / 3) / t.
+
+The matrix (8.6 GB) is far larger than L2 (129 MB), so no flush is needed
+between steps.  `value` is timed with CUDA events on the launching stream;
+`e2e` times the host-buffer public call lu_factor_host (pinned host copy in,
+factor, L\\U and pivots back to pinned host memory) the same way.
+
+--impl reference times the CPU oracle (plain C, FP64, the same tournament
+rule) on the host cores, on a bounded sample of the same workload.
+
+Multi-GPU: single-matrix LU does not shard; N ranks run N independent
+replicas (one matrix per GPU, no data-path collective) and `value` is the
+work of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LU TFLOP/s (2N^3/3) vs FP64 peak"
+UNIT = "TFLOP/s"
+# binary64 peak of the DFMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+# (the nominal 1.25 TFLOP/s per GPU at the maximum SM clock).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--b", type=int, default=256)
+    ap.add_argument("--h", type=int, default=128)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--cpu-sample-n", type=int, default=8192,
+                    help="order of the matrix the CPU oracle factors as its bounded sample")
+    ap.add_argument("--ref-sample-n", type=int, default=4096,
+                    help="order of the matrix the CPU oracle factors in each --impl reference step")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return f"dense FP64 LU, N={a.n}, b={a.b}, h={a.h}, N(0,1) entries, seed {a.seed}"
+
+
+def base_config(a):
+    return {"workload": workload_name(a), "n": a.n, "b": a.b, "h": a.h,
+            "l2_flush": "inputs larger than L2 (matrix 8.6 GB vs 129 MB L2)" if a.n >= 4096
+            else "no flush (matrix fits in L2)"}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+def oracle_sample(a, reps: int = 1):
+    import oracle
+    import workloads as wl
+    cores = oracle.set_threads(len(os.sched_getaffinity(0)))
+    ns = a.cpu_sample_n
+    A = wl.matrix_normal(ns, ns, seed=a.seed)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.lu_factor(A, b=a.b, h=a.h)
+        times.append(time.perf_counter() - t0)
+    flops = 2.0 * ns ** 3 / 3.0
+    return {"value": flops / min(times) / 1e12, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one oracle factorization of an N={ns} N(0,1) matrix (b={a.b}, h={a.h}), "
+                      f"{2 * ns ** 3 / 3:.3e} flop, best of {reps}, {cores} threads",
+            "seconds": min(times)}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import workloads as wl
+    oracle.build()
+    cores = oracle.set_threads(len(os.sched_getaffinity(0)))
+    ns = a.ref_sample_n
+    A = wl.matrix_normal(ns, ns, seed=a.seed)
+    flops = 2.0 * ns ** 3 / 3.0
+    for _ in range(a.warmup):
+        oracle.lu_factor(A, b=a.b, h=a.h)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle.lu_factor(A, b=a.b, h=a.h)
+    t = time.perf_counter() - t0
+    val = a.steps * flops / t / 1e12
+    cfg = base_config(a)
+    cfg["cpu_sample_n"] = ns
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "impl": "reference", "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"each step one oracle factorization of an N={ns} N(0,1) matrix "
+                                      f"(b={a.b}, h={a.h}) on {cores} threads"},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "gpu_launches": 0}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def traffic_per_launch(avg_flops_per_launch: float):
+    """DRAM bytes per Schur launch from the committed ncu summary, scaled by
+    algorithmic work, or None when the kernel source changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get("schur_f64")
+        src = open(os.path.join(ROOT, "paper_2010_05975_gb300", "csrc", "schur_f64.cu"), "rb").read()
+        if not rec or rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return rec["dram_bytes_per_flop"] * avg_flops_per_launch
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2010_05975_gb300 as g
+    from paper_2010_05975_gb300 import build as nb
+    nb.build()
+    import workloads as wl
+
+    n, b, h = a.n, a.b, a.h
+    flops = 2.0 * n ** 3 / 3.0
+    A_np = wl.matrix_normal(n, n, seed=a.seed)
+    hA = torch.from_numpy(A_np).pin_memory()
+    del A_np
+    dA0 = hA.to(dev)
+    dA = torch.empty_like(dA0)
+    piv = torch.empty(n, dtype=torch.int32, device=dev)
+    info = torch.empty(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        dA.copy_(dA0)
+        g.lu_factor_ex(dA, b=b, h=h, piv=piv, info=info, stream=stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if int(info.cpu()[0]) != 0:
+        raise RuntimeError(f"factorization reported info={int(info.cpu()[0])}")
+
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    g.prof_begin()
+    l0 = g.kernel_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = g.kernel_launch_count() - l0
+    prof = g.prof_end()
+    clk = clocks.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    tmax = t
+    if world > 1:
+        tt = torch.tensor([t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tmax = float(tt.item())
+        lt = torch.tensor([launches], dtype=torch.int64, device=dev)
+        dist.all_reduce(lt)
+        launches = int(lt.item())
+        dist.barrier()
+    value = world * a.steps * flops / tmax / 1e12
+
+    # end to end through the host-buffer public call
+    hout = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    ke = max(1, a.e2e_steps)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(ke):
+        _, piv_h, info_h = g.lu_factor_host(hA, b=b, h=h, out=hout, device=dev, stream=stream)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    te = f0.elapsed_time(f1) / 1e3
+    if world > 1:
+        tt = torch.tensor([te], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+    e2e = {"value": world * ke * flops / te / 1e12, "unit": UNIT, "steps": ke,
+           "h2d_bytes_per_step": int(hA.numel() * 8),
+           "d2h_bytes_per_step": int(hout.numel() * 8 + piv_h.numel() * 4 + 4)}
+
+    sch = prof.get("schur_f64", {"launches": 0, "ms": 0.0, "flops": 0.0})
+    roof = None
+    if sch["launches"]:
+        ach = sch["flops"] / (sch["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": traffic_per_launch(sch["flops"] / sch["launches"]),
+                "kernel": "schur_f64_kernel", "launches": sch["launches"],
+                "avg_launch_ms": sch["ms"] / sch["launches"],
+                "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; the probe measured 1.19"}
+    shares = {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof.items()}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1:
+        import oracle
+        oracle.build()
+        cpu = oracle_sample(a)
+    cfg = base_config(a)
+    cfg["parallelism"] = "replicas" if world > 1 else "single GPU"
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": 1e3 * tmax / a.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": cfg, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+           "gpu_launches": launches, "kernel_time_ms": shares}
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -109,6 +109,44 @@ int lu_factor_ex(int m, int n, double *A, int lda, int *piv, int *info,
 int lu_solve(int n, int nrhs, const double *LU, int lda, const int *piv,
              double *B, int ldb, cudaStream_t stream);
 
+
+/* ---------------------------------------------------------------------------
+ * Measurement hooks (no counterpart in the paper's algorithm: they time it).
+ * While a session is open, every kernel launch of the library is bracketed
+ * by CUDA events recorded on the launch's stream; lu_prof_end waits for
+ * those events and returns, per launch class, the launch count, the summed
+ * event time and the summed algorithmic work (flops; bytes where a class is
+ * memory-bound).  Process-wide, one session at a time, host thread-safe.
+ * ------------------------------------------------------------------------- */
+#define LU_PROF_TSLU      0   /* tournament levels (TournPivot)                 */
+#define LU_PROF_PIVOT     1   /* pivot bookkeeping and row moves                */
+#define LU_PROF_TRSM_L21  2   /* FactorizeA10                                    */
+#define LU_PROF_TRSM_U12  3   /* FactorizeA01                                    */
+#define LU_PROF_SCHUR     4   /* FactorizeA11, binary64                          */
+#define LU_PROF_SCHUR_LP  5   /* FactorizeA11, bf16/fp8 tensor cores             */
+#define LU_PROF_SOLVE     6   /* getrs kernels                                   */
+#define LU_PROF_RESIDUAL  7   /* binary64 residual and backward error            */
+#define LU_PROF_OTHER     8   /* conversions, copies, scaling                    */
+#define LU_PROF_NCLASS    9
+
+typedef struct {
+    int kernel_class;        /* LU_PROF_*                                        */
+    int launches;            /* launches recorded                                */
+    double total_ms;         /* summed CUDA-event time of those launches         */
+    double total_flops;      /* summed algorithmic flops                         */
+    double total_bytes;      /* summed algorithmic bytes                         */
+} lu_prof_entry;
+
+/* Open a session (discarding any previous records).  Returns 0. */
+int lu_prof_begin(void);
+/* Close the session: synchronises the recorded events and writes up to
+ * max_entries non-empty classes to out (host array), their number to
+ * *n_entries (host).  Returns 0, -2/-3 on bad arguments, LU_ELAUNCH if an
+ * event failed. */
+int lu_prof_end(lu_prof_entry *out, int max_entries, int *n_entries);
+/* Kernels launched by this library in this process so far. */
+unsigned long long lu_kernel_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,4 +26,8 @@ from .api import (  # noqa: F401
     lu_factor,
     lu_factor_ex,
     lu_solve,
+    lu_factor_host,
+    prof_begin,
+    prof_end,
+    kernel_launch_count,
 )

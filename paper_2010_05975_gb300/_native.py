@@ -35,6 +35,13 @@ class lu_opts(ctypes.Structure):
                 ("reserved", ctypes.c_int * 5)]
 
 
+class lu_prof_entry(ctypes.Structure):
+    _fields_ = [("kernel_class", ctypes.c_int), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double),
+                ("total_flops", ctypes.c_double), ("total_bytes", ctypes.c_double)]
+
+
+PROF_CLASSES = ["tslu", "pivot", "trsm_l21", "trsm_u12", "schur_f64", "schur_lowp", "solve", "residual", "other"]
+
 _lock = threading.Lock()
 _lib = None
 
@@ -46,6 +53,9 @@ _SIGS = {
     "lu_factor": ([I, P, I, P, P, P], I),
     "lu_factor_ex": ([I, I, P, I, P, P, ctypes.POINTER(lu_opts), P], I),
     "lu_solve": ([I, I, P, I, P, P, I, P], I),
+    "lu_prof_begin": ([], I),
+    "lu_prof_end": ([P, I, P], I),
+    "lu_kernel_launch_count": ([], ctypes.c_ulonglong),
 }
 
 

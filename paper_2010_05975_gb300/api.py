@@ -73,3 +73,51 @@ def lu_solve(LU: torch.Tensor, piv: torch.Tensor, B: torch.Tensor, stream=None) 
                       max(B2.stride(0), 1), _stream_handle(stream))
     nat.check("lu_solve", rc)
     return B
+
+
+def prof_begin() -> None:
+    nat.check("lu_prof_begin", nat.library().lu_prof_begin())
+
+
+def prof_end() -> dict:
+    """Close a profiling session; returns {class: {launches, ms, flops, bytes}}."""
+    arr = (nat.lu_prof_entry * 16)()
+    n = ctypes.c_int(0)
+    nat.check("lu_prof_end", nat.library().lu_prof_end(arr, 16, ctypes.byref(n)))
+    out = {}
+    for i in range(n.value):
+        e = arr[i]
+        out[nat.PROF_CLASSES[e.kernel_class]] = {"launches": e.launches, "ms": e.total_ms,
+                                                 "flops": e.total_flops, "bytes": e.total_bytes}
+    return out
+
+
+def kernel_launch_count() -> int:
+    return int(nat.library().lu_kernel_launch_count())
+
+
+def lu_factor_host(A_host: torch.Tensor, b: int = 0, h: int = 0, out: torch.Tensor | None = None,
+                   device: torch.device | str | None = None, stream=None):
+    """Factor a matrix that lives in host memory: copy it to the device, run
+    lu_factor_ex there, copy L\\U and the pivots back.  A_host is a row-major
+    float64 CPU tensor (pinned memory makes the copies asynchronous); the
+    result goes to `out` (a CPU tensor, allocated when None).  Returns
+    (out, piv_host, info)."""
+    if A_host.is_cuda or A_host.dtype != torch.float64 or A_host.dim() != 2:
+        raise TypeError("A_host must be a 2-D float64 CPU tensor")
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    m, n = A_host.shape
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.stream(s):
+        dA = torch.empty((m, n), dtype=torch.float64, device=dev)
+        dA.copy_(A_host, non_blocking=True)
+        piv, info = lu_factor_ex(dA, b=b, h=h, stream=s)
+        if out is None:
+            out = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+        out.copy_(dA, non_blocking=True)
+        piv_h = torch.empty(piv.shape, dtype=torch.int32, pin_memory=True)
+        info_h = torch.empty(1, dtype=torch.int32, pin_memory=True)
+        piv_h.copy_(piv, non_blocking=True)
+        info_h.copy_(info, non_blocking=True)
+    s.synchronize()
+    return out, piv_h, int(info_h[0])

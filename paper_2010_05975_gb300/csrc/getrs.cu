@@ -10,6 +10,7 @@
 //    remain.
 // 3. Y is copied back into B.
 #include "common.cuh"
+#include "prof.cuh"
 
 namespace lu {
 
@@ -124,25 +125,45 @@ int getrs_impl(int n, int nrhs, const T* LU, int lda, const int* piv, T* B, int 
         const size_t smem = static_cast<size_t>(n) * sizeof(int);
         LU_TRY(cudaFuncSetAttribute(perm_from_piv_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem)));
-        perm_from_piv_smem<<<1, 256, smem, s>>>(n, piv, perm);
+        {
+            ProfScope ps(LU_PROF_SOLVE, s);
+            perm_from_piv_smem<<<1, 256, smem, s>>>(n, piv, perm);
+            count_launches(1);
+        }
     } else {
-        perm_from_piv_global<<<1, 256, 0, s>>>(n, piv, perm);
+        {
+            ProfScope ps(LU_PROF_SOLVE, s);
+            perm_from_piv_global<<<1, 256, 0, s>>>(n, piv, perm);
+            count_launches(1);
+        }
     }
     LU_LAUNCHED();
     const long long tot = static_cast<long long>(n) * nrhs;
     const int gblocks = static_cast<int>(tot / 256 + 1 < 4096 ? tot / 256 + 1 : 4096);
-    gather_rows<T><<<gblocks, 256, 0, s>>>(n, nrhs, perm, B, ldb, Y);
+    {
+        ProfScope ps(LU_PROF_SOLVE, s);
+        gather_rows<T><<<gblocks, 256, 0, s>>>(n, nrhs, perm, B, ldb, Y);
+        count_launches(1);
+    }
     LU_LAUNCHED();
     const size_t usmem = static_cast<size_t>(kSolveNB) * nrhs * sizeof(T);
     LU_TRY(cudaFuncSetAttribute(block_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(usmem)));
     for (int r0 = 0; r0 < n; r0 += kSolveNB) {
         const int nb = min(kSolveNB, n - r0);
-        diag_solve<T, true><<<1, 64, 0, s>>>(nrhs, r0, nb, LU, lda, Y);
+        {
+            ProfScope ps(LU_PROF_SOLVE, s);
+            diag_solve<T, true><<<1, 64, 0, s>>>(nrhs, r0, nb, LU, lda, Y);
+            count_launches(1);
+        }
         LU_LAUNCHED();
         const int rows = n - (r0 + nb);
         if (rows > 0) {
             const int blocks = min(cdiv(rows, 8), 2 * 152);
-            block_update<T><<<blocks, 256, usmem, s>>>(nrhs, r0 + nb, n, r0, nb, LU, lda, Y);
+            {
+                ProfScope ps(LU_PROF_SOLVE, s);
+                block_update<T><<<blocks, 256, usmem, s>>>(nrhs, r0 + nb, n, r0, nb, LU, lda, Y);
+                count_launches(1);
+            }
             LU_LAUNCHED();
         }
     }
@@ -150,15 +171,27 @@ int getrs_impl(int n, int nrhs, const T* LU, int lda, const int* piv, T* B, int 
     for (int bi = nblk - 1; bi >= 0; --bi) {
         const int r0 = bi * kSolveNB;
         const int nb = min(kSolveNB, n - r0);
-        diag_solve<T, false><<<1, 64, 0, s>>>(nrhs, r0, nb, LU, lda, Y);
+        {
+            ProfScope ps(LU_PROF_SOLVE, s);
+            diag_solve<T, false><<<1, 64, 0, s>>>(nrhs, r0, nb, LU, lda, Y);
+            count_launches(1);
+        }
         LU_LAUNCHED();
         if (r0 > 0) {
             const int blocks = min(cdiv(r0, 8), 2 * 152);
-            block_update<T><<<blocks, 256, usmem, s>>>(nrhs, 0, r0, r0, nb, LU, lda, Y);
+            {
+                ProfScope ps(LU_PROF_SOLVE, s);
+                block_update<T><<<blocks, 256, usmem, s>>>(nrhs, 0, r0, r0, nb, LU, lda, Y);
+                count_launches(1);
+            }
             LU_LAUNCHED();
         }
     }
-    copy_out<T><<<gblocks, 256, 0, s>>>(n, nrhs, Y, B, ldb);
+    {
+        ProfScope ps(LU_PROF_SOLVE, s);
+        copy_out<T><<<gblocks, 256, 0, s>>>(n, nrhs, Y, B, ldb);
+        count_launches(1);
+    }
     LU_LAUNCHED();
     return 0;
 }

@@ -8,6 +8,7 @@
 // and receives fma(-l, u, acc) for p = 0, 1, ..., w-1, the oracle's order, so
 // the result is bit-identical to it.
 #include "common.cuh"
+#include "prof.cuh"
 
 namespace lu {
 
@@ -100,7 +101,11 @@ int schur_f64(double* A, int lda, int m, int n, int k, int w, cudaStream_t s) {
     // The DFMA pipe (about 2 FMA/clk/SM) is the bound at any tile size; 64 x 64
     // tiles keep 88 registers per thread, two CTAs per SM and a short tail.
     dim3 grid(cdiv(N, 64), cdiv(M, 64));
-    schur_f64_kernel<64, 64><<<grid, 256, 0, s>>>(A, lda, m, n, k, w);
+    {
+        ProfScope ps(LU_PROF_SCHUR, s, 2.0 * M * N * w, 8.0 * (2.0 * M * N + static_cast<double>(M + N) * w));
+        schur_f64_kernel<64, 64><<<grid, 256, 0, s>>>(A, lda, m, n, k, w);
+        count_launches(1);
+    }
     LU_LAUNCHED();
     return 0;
 }

@@ -6,6 +6,7 @@
 // then (L21 only) one IEEE division: the same operation sequence as the
 // column-by-column and row-by-row forms of the definition.
 #include "common.cuh"
+#include "prof.cuh"
 
 namespace lu {
 
@@ -68,7 +69,11 @@ int trsm_l21_f64(double* A, int lda, int m, int k, int w, cudaStream_t s) {
     if (rows <= 0) return 0;
     const size_t smem = static_cast<size_t>(w) * kL21Stride * sizeof(double);
     LU_TRY(cudaFuncSetAttribute(trsm_l21_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    trsm_l21_kernel<<<cdiv(rows, kL21Rows), 256, smem, s>>>(A, lda, m, k, w);
+    {
+        ProfScope ps(LU_PROF_TRSM_L21, s, static_cast<double>(rows) * w * w);
+        trsm_l21_kernel<<<cdiv(rows, kL21Rows), 256, smem, s>>>(A, lda, m, k, w);
+        count_launches(1);
+    }
     LU_LAUNCHED();
     return 0;
 }
@@ -78,7 +83,11 @@ int trsm_u12_f64(double* A, int lda, int n, int k, int w, cudaStream_t s) {
     if (cols <= 0 || w <= 1) return 0;
     const size_t smem = static_cast<size_t>(w) * kU12Cols * sizeof(double);
     LU_TRY(cudaFuncSetAttribute(trsm_u12_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    trsm_u12_kernel<<<cdiv(cols, kU12Cols), 256, smem, s>>>(A, lda, n, k, w);
+    {
+        ProfScope ps(LU_PROF_TRSM_U12, s, static_cast<double>(cols) * w * (w - 1));
+        trsm_u12_kernel<<<cdiv(cols, kU12Cols), 256, smem, s>>>(A, lda, n, k, w);
+        count_launches(1);
+    }
     LU_LAUNCHED();
     return 0;
 }

@@ -14,6 +14,7 @@
 // nodes keep all their rows, are skipped: the first launched level takes
 // contiguous row ranges of H rows.
 #include "common.cuh"
+#include "prof.cuh"
 #include <cooperative_groups.h>
 #include <climits>
 
@@ -260,7 +261,9 @@ static int launch_level(const LevelArgs& args, int nnode, int C, size_t smem, cu
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    ProfScope ps(LU_PROF_TSLU, s);
     LU_TRY(cudaLaunchKernelEx(&cfg, tslu_level_kernel, args));
+    count_launches(1);
     return 0;
 }
 
@@ -405,11 +408,19 @@ __global__ void __launch_bounds__(256) row_move_kernel(double* __restrict__ A, i
 int pivot_apply_f64(double* A, int lda, int m, int n, int k, int w, const int* root_list, const double* a00,
                     int* piv, int* mv, cudaStream_t s) {
     (void)m;
-    pivot_moves_kernel<<<1, 256, 0, s>>>(root_list, k, w, piv, mv);
+    {
+        ProfScope ps(LU_PROF_PIVOT, s);
+        pivot_moves_kernel<<<1, 256, 0, s>>>(root_list, k, w, piv, mv);
+        count_launches(1);
+    }
     LU_LAUNCHED();
     const size_t smem = static_cast<size_t>(2 * w) * 32 * sizeof(double);
     LU_TRY(cudaFuncSetAttribute(row_move_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    row_move_kernel<<<cdiv(n, 32), 256, smem, s>>>(A, lda, n, k, w, mv, a00);
+    {
+        ProfScope ps(LU_PROF_PIVOT, s);
+        row_move_kernel<<<cdiv(n, 32), 256, smem, s>>>(A, lda, n, k, w, mv, a00);
+        count_launches(1);
+    }
     LU_LAUNCHED();
     return 0;
 }

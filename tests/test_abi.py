@@ -17,7 +17,7 @@ def declared_functions():
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
-        for m in re.finditer(r"^\s*(?:int|void|size_t|const char\s*\*)\s+(\w+)\s*\(", src, flags=re.M):
+        for m in re.finditer(r"^\s*(?:int|void|size_t|double|unsigned long long|const char\s*\*)\s+\**(\w+)\s*\(", src, flags=re.M):
             names.add(m.group(1))
     return sorted(names)
 
