@@ -162,7 +162,7 @@ def run_reference(a):
     t = time.perf_counter() - t0
     val = a.steps * flops / t / 1e12
     cfg = base_config(a)
-    cfg["cpu_sample_n"] = ns
+    cfg["ref_sample_n"] = ns
     out = {"metric": METRIC, "value": val, "unit": UNIT, "impl": "reference", "n_gpus": a.gpus,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,

@@ -42,28 +42,68 @@ constexpr size_t kTsluSmemLimit = 232448 - 2048;
 static bool tslu_shapes_fit(int m, int kmax, int b, int h) {
     for (int k = 0; k < kmax; k += b) {
         const int w = (kmax - k) < b ? (kmax - k) : b;
-        if (tslu_shape(m, k, w, h).smem > kTsluSmemLimit) return false;
+        if (tslu_shape(m, k, w, h, kTsluMaxCluster).smem > kTsluSmemLimit) return false;
     }
     return true;
 }
 
+// Step loop with a one-panel lookahead.  On the caller's stream s, step t
+// runs: wait for its tournament -> apply pivots -> L21, U12 -> the Schur
+// update of the NEXT panel's columns -> (fork) the rest of the Schur update.
+// The next tournament reads only those panel columns, so it runs on a
+// high-priority side stream concurrently with the rest of the update; the
+// next step's pivot application waits for both.
 static int factor_f64(int m, int n, double* A, int lda, int* piv, int* info, int b, int h, cudaStream_t s) {
     LU_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
     const int kmax = m < n ? m : n;
     if (kmax == 0) return 0;
     FactorWs ws;
     if (int rc = ws_alloc(ws, m, b, h, s)) return rc;
+    int lo = 0, hi = 0;
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_panel = nullptr, ev_tslu = nullptr;
     int rc = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_tslu, cudaEventDisableTiming) != cudaSuccess)
+        rc = LU_ELAUNCH;
+    const int* root = nullptr;
+    if (!rc && cudaEventRecord(ev_panel, s) != cudaSuccess) rc = LU_ELAUNCH;
+    if (!rc && cudaStreamWaitEvent(s2, ev_panel, 0) != cudaSuccess) rc = LU_ELAUNCH;
+    if (!rc) rc = tslu_select_f64(A, lda, m, 0, (kmax < b ? kmax : b), h, ws.lists, ws.counts, ws.stride_nodes,
+                                  ws.a00, info, &root, s2);
+    if (!rc && cudaEventRecord(ev_tslu, s2) != cudaSuccess) rc = LU_ELAUNCH;
     for (int k = 0; k < kmax && rc == 0; k += b) {
         const int w = (kmax - k) < b ? (kmax - k) : b;
-        const int* root = nullptr;
-        rc = tslu_select_f64(A, lda, m, k, w, h, ws.lists, ws.counts, ws.stride_nodes, ws.a00, info, &root, s);
-        if (!rc) rc = pivot_apply_f64(A, lda, m, n, k, w, root, ws.a00, piv, ws.mv, s);
+        const int kn = k + w;
+        const int wn = (kmax - kn) < b ? (kmax - kn) : b;     // next panel width (<= 0: none)
+        if (cudaStreamWaitEvent(s, ev_tslu, 0) != cudaSuccess) { rc = LU_ELAUNCH; break; }
+        rc = pivot_apply_f64(A, lda, m, n, k, w, root, ws.a00, piv, ws.mv, s);
         if (!rc) rc = trsm_l21_f64(A, lda, m, k, w, s);
         if (!rc) rc = trsm_u12_f64(A, lda, n, k, w, s);
-        if (!rc) rc = schur_f64(A, lda, m, n, k, w, s);
+        if (rc) break;
+        if (wn > 0) {
+            rc = schur_f64(A, lda, m, k, w, kn, kn + wn, s);
+            if (!rc && cudaEventRecord(ev_panel, s) != cudaSuccess) rc = LU_ELAUNCH;
+            if (!rc && cudaStreamWaitEvent(s2, ev_panel, 0) != cudaSuccess) rc = LU_ELAUNCH;
+            if (!rc) rc = tslu_select_f64(A, lda, m, kn, wn, h, ws.lists, ws.counts, ws.stride_nodes, ws.a00,
+                                          info, &root, s2);
+            if (!rc && cudaEventRecord(ev_tslu, s2) != cudaSuccess) rc = LU_ELAUNCH;
+            if (!rc) rc = schur_f64(A, lda, m, k, w, kn + wn, n, s);
+        } else {
+            rc = schur_f64(A, lda, m, k, w, kn, n, s);
+        }
+    }
+    // join the side stream before the workspace goes back to the pool
+    if (ev_tslu && s2) {
+        cudaEventRecord(ev_tslu, s2);
+        cudaStreamWaitEvent(s, ev_tslu, 0);
     }
     ws_free(ws, s);
+    if (ev_panel) cudaEventDestroy(ev_panel);
+    if (ev_tslu) cudaEventDestroy(ev_tslu);
+    if (s2) cudaStreamDestroy(s2);
     return rc;
 }
 

@@ -44,7 +44,8 @@ struct TsluShape {
 // upward until a node holds more than w rows: selection is independent of
 // the order in which candidate rows are stacked, so a node made only of
 // such leaves selects from its whole contiguous row range.
-TsluShape tslu_shape(int m, int k, int w, int h);
+TsluShape tslu_shape(int m, int k, int w, int h, int max_cluster);
+int tslu_max_cluster();
 
 // Host entry points of the FP64 pieces (stream-ordered, no sync).
 int tslu_select_f64(const double* A, int lda, int m, int k, int w, int h,
@@ -55,7 +56,8 @@ int pivot_apply_f64(double* A, int lda, int m, int n, int k, int w,
                     int* mv, cudaStream_t s);
 int trsm_l21_f64(double* A, int lda, int m, int k, int w, cudaStream_t s);
 int trsm_u12_f64(double* A, int lda, int n, int k, int w, cudaStream_t s);
-int schur_f64(double* A, int lda, int m, int n, int k, int w, cudaStream_t s);
+// A[r0:m, c0:c1) -= A[r0:m, k:k+w) * A[k:k+w, c0:c1)   (r0 = k + w)
+int schur_f64(double* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s);
 int getrs_f64(int n, int nrhs, const double* LU, int lda, const int* piv,
               double* B, int ldb, cudaStream_t s);
 

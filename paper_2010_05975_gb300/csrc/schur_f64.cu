@@ -13,7 +13,8 @@
 namespace lu {
 
 template <int BM, int BN>
-__global__ void __launch_bounds__(256) schur_f64_kernel(double* __restrict__ A, int lda, int m, int n, int k, int w) {
+__global__ void __launch_bounds__(256) schur_f64_kernel(double* __restrict__ A, int lda, int m, int k, int w, int c0,
+                                                        int n) {
     constexpr int BK = 8;
     constexpr int TM = BM / 16, TN = BN / 16;
     constexpr int APT = BM * BK / 256;          // A elements loaded per thread per chunk
@@ -24,7 +25,7 @@ __global__ void __launch_bounds__(256) schur_f64_kernel(double* __restrict__ A, 
 
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     const int row0 = k + w + blockIdx.y * BM;
-    const int col0 = k + w + blockIdx.x * BN;
+    const int col0 = c0 + blockIdx.x * BN;
 
     double acc[TM][TN];
 #pragma unroll
@@ -95,15 +96,15 @@ __global__ void __launch_bounds__(256) schur_f64_kernel(double* __restrict__ A, 
         }
 }
 
-int schur_f64(double* A, int lda, int m, int n, int k, int w, cudaStream_t s) {
-    const int M = m - k - w, N = n - k - w;
+int schur_f64(double* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s) {
+    const int M = m - k - w, N = c1 - c0;
     if (M <= 0 || N <= 0 || w <= 0) return 0;
     // The DFMA pipe (about 2 FMA/clk/SM) is the bound at any tile size; 64 x 64
     // tiles keep 88 registers per thread, two CTAs per SM and a short tail.
     dim3 grid(cdiv(N, 64), cdiv(M, 64));
     {
         ProfScope ps(LU_PROF_SCHUR, s, 2.0 * M * N * w, 8.0 * (2.0 * M * N + static_cast<double>(M + N) * w));
-        schur_f64_kernel<64, 64><<<grid, 256, 0, s>>>(A, lda, m, n, k, w);
+        schur_f64_kernel<64, 64><<<grid, 256, 0, s>>>(A, lda, m, k, w, c0, c1);
         count_launches(1);
     }
     LU_LAUNCHED();

@@ -22,7 +22,7 @@ namespace cg = cooperative_groups;
 
 namespace lu {
 
-TsluShape tslu_shape(int m, int k, int w, int h) {
+TsluShape tslu_shape(int m, int k, int w, int h, int max_cluster) {
     TsluShape s{};
     const int nact = m - k;
     int H = h;
@@ -34,7 +34,7 @@ TsluShape tslu_shape(int m, int k, int w, int h) {
     s.nsuper = cdiv(nact, H);
     s.nr_max = (s.nsuper == 1) ? nact : (H > 2 * w ? H : 2 * w);
     int C = 1, R = s.nr_max;
-    while (C < kTsluMaxCluster && static_cast<long long>(R) * (w + 1) > 8192) {
+    while (C < max_cluster && static_cast<long long>(R) * (w + 1) > 4096) {
         C *= 2;
         R = cdiv(s.nr_max, C);
     }
@@ -217,14 +217,16 @@ __global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs a) {
             if (owner == q) ord[lr] = c;
         }
         __syncthreads();
-        // 4. multipliers and rank-1 update of the unchosen local rows
+        // 4. multipliers (one row per lane: the IEEE division is the costly
+        //    binary64 operation) and rank-1 update of the unchosen local rows
         const double pv = prow[c];
         if (pv != 0.0) {
+            for (int r = tid; r < nloc; r += blockDim.x)
+                if (ord[r] < 0) W[r * ws + c] = W[r * ws + c] / pv;
+            __syncthreads();
             for (int r = warp; r < nloc; r += nwarp) {
                 if (ord[r] >= 0) continue;
-                const double l = W[r * ws + c] / pv;
-                __syncwarp();
-                if (lane == 0) W[r * ws + c] = l;
+                const double l = W[r * ws + c];
                 for (int j = c + 1 + lane; j < w; j += 32) W[r * ws + j] = fma(-l, prow[j], W[r * ws + j]);
             }
         } else if (tid == 0 && s_zero < 0) {
@@ -267,9 +269,40 @@ static int launch_level(const LevelArgs& args, int nnode, int C, size_t smem, cu
     return 0;
 }
 
+// Largest cluster the device runs for the tournament kernel: 16 where the
+// non-portable size is available, else the portable 8.
+int tslu_max_cluster() {
+    static int cached = 0;
+    if (cached) return cached;
+    int best = kTsluMaxCluster;
+    if (cudaFuncSetAttribute(tslu_level_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        const TsluShape sh = tslu_shape(2 * kMaxPanel * 16, 0, kMaxPanel, 128, 16);
+        if (cudaFuncSetAttribute(tslu_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(sh.smem)) == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(16);
+            cfg.blockDim = dim3(kTsluThreads);
+            cfg.dynamicSmemBytes = sh.smem;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 16;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, tslu_level_kernel, &cfg) == cudaSuccess && nclusters > 0)
+                best = 16;
+        }
+    }
+    cudaGetLastError();
+    cached = best;
+    return cached;
+}
+
 int tslu_select_f64(const double* A, int lda, int m, int k, int w, int h, int* lists, int* counts,
                     size_t list_stride_nodes, double* a00, int* info, const int** root_list, cudaStream_t s) {
-    const TsluShape sh = tslu_shape(m, k, w, h);
+    const TsluShape sh = tslu_shape(m, k, w, h, tslu_max_cluster());
     LU_TRY(cudaFuncSetAttribute(tslu_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(sh.smem)));
     int* list_buf[2] = {lists, lists + list_stride_nodes * w};
