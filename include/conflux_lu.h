@@ -110,6 +110,91 @@ int lu_solve(int n, int nrhs, const double *LU, int lda, const int *piv,
              double *B, int ldb, cudaStream_t stream);
 
 
+/*
+ * lu_factor_f32 -- the same factorization on a binary32 matrix.
+ * opts->precision selects the Schur-update arithmetic:
+ *   LU_PREC_F32 (default)  binary32 everywhere;
+ *   LU_PREC_BF16 / FP8     binary32 panel, pivoting and triangular solves;
+ *                          the trailing update takes bfloat16 / fp8-e4m3
+ *                          operands (fp8: one power-of-two scale per 256 x 256
+ *                          operand tile) with fp32 accumulation on the
+ *                          tensor cores.  Needs m == n and b a multiple of
+ *                          128 (else LU_EUNSUPPORTED).
+ * A negative *info (-LU_ETIMEOUT) reports a device-side wait that ran out;
+ * the factors are then invalid.
+ */
+int lu_factor_f32(int m, int n, float *A, int lda, int *piv, int *info,
+                  const lu_opts *opts, cudaStream_t stream);
+
+/* lu_solve_f32 -- X = U^{-1} L^{-1} P B with binary32 factors (B overwritten). */
+int lu_solve_f32(int n, int nrhs, const float *LU, int lda, const int *piv,
+                 float *B, int ldb, cudaStream_t stream);
+
+/*
+ * lu_gemm_lowp -- the low-precision Schur update on its own:
+ *   C -= sL * sU * round(L / sL) * round(U / sU)
+ * L: M x K (ldl), U: K x N (ldu), C: M x N (ldc), all binary32 device
+ * arrays, K <= 256.  round = bfloat16 (precision LU_PREC_BF16, scales 1) or
+ * fp8 e4m3 with saturation (LU_PREC_FP8; sL per 256 rows of L, sU per 256
+ * columns of U, each the smallest power of two with max|block| / s <= 448).
+ * Products accumulate in fp32 on the tensor cores.  status (device int) is
+ * 0, or -LU_ETIMEOUT if a device-side wait ran out.
+ */
+int lu_gemm_lowp(int M, int N, int K, const float *L, int ldl, const float *U,
+                 int ldu, float *C, int ldc, int precision, int *status,
+                 cudaStream_t stream);
+
+/*
+ * lu_residual -- R = B - A X in binary64 and, per column c, the normwise
+ * backward error eta[c] = ||r_c||_inf / (||A||_inf ||x_c||_inf + ||b_c||_inf).
+ * A: n x n (lda); X, B, R: n x nrhs (ldx, ldb, ldr); eta: device double[nrhs].
+ */
+int lu_residual(int n, int nrhs, const double *A, int lda, const double *X,
+                int ldx, const double *B, int ldb, double *R, int ldr,
+                double *eta, cudaStream_t stream);
+
+/* Options and result of ir_solve.  Zero fields take defaults. */
+typedef struct {
+    int precision;          /* first factorization: LU_PREC_BF16 (also when 0),
+                               LU_PREC_FP8 or LU_PREC_F32                      */
+    int b, h;               /* panel width and leaf height (defaults 256/128 for
+                               n >= 4096, else 128/128)                        */
+    double tol;             /* stop when max_c eta_c <= tol (default 1e-12)    */
+    int max_iter;           /* outer refinement steps (default 40)             */
+    int gmres_restart;      /* FGMRES restart length (default 30, max 200)     */
+    int reserved[4];        /* must be zero                                     */
+} ir_opts;
+
+typedef struct {
+    int iters;              /* outer refinement steps taken                    */
+    int gmres_iters;        /* inner FGMRES iterations in total                */
+    int path;               /* 0: classical refinement converged; 1: FGMRES-IR
+                               converged; -1: tol not reached                  */
+    int info;               /* info of the factorization                        */
+    double eta;             /* final max_c eta_c                                */
+    double eta0;            /* max_c eta_c of the first solve                   */
+    int precision;          /* factorization precision in use at the end        */
+    int refactors;          /* times the ladder moved up a precision            */
+} ir_result;
+
+/*
+ * ir_solve -- solve A X = B to binary64 backward error tol with a
+ * low-precision factorization and binary64 refinement.  A (n x n, lda) and
+ * B (n x nrhs, ldb) are read only; X (n x nrhs, ldx) receives the solution;
+ * all three are device arrays.  res is a HOST pointer.  The refinement
+ * decides on the host when to stop, so this call synchronizes `stream` and
+ * returns when X is final.  Classical refinement (x += LU^{-1} r) runs while
+ * each step cuts eta by 4x or more; after that the correction equation is
+ * solved by right-preconditioned flexible GMRES (binary64 Arnoldi and
+ * Gram-Schmidt, the fp32 LU solve as preconditioner).  When an FGMRES cycle
+ * gains less than 10x, or two cycles do not reach tol, the matrix is
+ * refactored one precision up (fp8 -> bf16 -> fp32) and refinement goes on
+ * from the current X.  max_iter bounds the refinement steps over all levels.
+ */
+int ir_solve(int n, int nrhs, const double *A, int lda, const double *B,
+             int ldb, double *X, int ldx, const ir_opts *opts,
+             ir_result *res, cudaStream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Measurement hooks (no counterpart in the paper's algorithm: they time it).
  * While a session is open, every kernel launch of the library is bracketed

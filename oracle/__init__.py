@@ -16,6 +16,13 @@ Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
   systems.
 * ``backward_error`` -- pinned against closed forms (exact solutions give 0,
   hand-computed small cases).
+* ``lu_factor_f32`` / ``lu_solve_f32`` -- the same code instantiated for
+  binary32; pinned by LAPACK sgetrf (b = 1) and exact dyadic L*U products.
+* ``round_lowp``     -- pinned against torch's bfloat16 / float8_e4m3fn
+  conversions (round to nearest even) and hand-worked ties and saturation.
+* ``e4m3_exponent``, ``gemm_lowp`` -- pinned by hand-worked exponents and by
+  exactly representable operands, where the update equals the binary64
+  product.
 """
 from .oracle import (  # noqa: F401
     build,
@@ -25,4 +32,9 @@ from .oracle import (  # noqa: F401
     tslu_select,
     backward_error,
     set_threads,
+    lu_factor_f32,
+    lu_solve_f32,
+    round_lowp,
+    e4m3_exponent,
+    gemm_lowp,
 )

@@ -58,287 +58,28 @@ typedef struct {
     long long s2_fma;
 } oracle_counts;
 
-/* ------------------------------------------------------------------------ */
-/* Local LUP candidate selection (Section 7.3).  rows[0..nr) are row          */
-/* positions of A; the panel is columns [k, k+w).  sel receives min(nr, w)    */
-/* row positions in pivot order.                                              */
-/* ------------------------------------------------------------------------ */
-static void gepp_select(const double *A, int lda, int k, int w,
-                        const int *rows, int nr, int *sel)
-{
-    double *W = (double *)malloc((size_t)nr * (size_t)w * sizeof(double));
-    int *id = (int *)malloc((size_t)nr * sizeof(int));
-    for (int i = 0; i < nr; ++i) {
-        id[i] = rows[i];
-        for (int j = 0; j < w; ++j)
-            W[(size_t)i * w + j] = IDX(A, lda, rows[i], k + j);
-    }
-    int ns = nr < w ? nr : w;
-    for (int c = 0; c < ns; ++c) {
-        /* argmax |W[i][c]| over i >= c; a tie goes to the smallest position */
-        int best = c;
-        double bv = fabs(W[(size_t)c * w + c]);
-        for (int i = c + 1; i < nr; ++i) {
-            double v = fabs(W[(size_t)i * w + c]);
-            if (v > bv || (v == bv && id[i] < id[best])) {
-                best = i;
-                bv = v;
-            }
-        }
-        if (best != c) {
-            for (int j = 0; j < w; ++j) {
-                double t = W[(size_t)c * w + j];
-                W[(size_t)c * w + j] = W[(size_t)best * w + j];
-                W[(size_t)best * w + j] = t;
-            }
-            int t = id[c];
-            id[c] = id[best];
-            id[best] = t;
-        }
-        double piv = W[(size_t)c * w + c];
-        if (piv != 0.0) {
-            for (int i = c + 1; i < nr; ++i) {
-                double l = W[(size_t)i * w + c] / piv;
-                W[(size_t)i * w + c] = l;
-                for (int j = c + 1; j < w; ++j)
-                    W[(size_t)i * w + j] = fma(-l, W[(size_t)c * w + j], W[(size_t)i * w + j]);
-            }
-        }
-    }
-    for (int i = 0; i < ns; ++i)
-        sel[i] = id[i];
-    free(W);
-    free(id);
-}
+void oracle_gemm_lowp(int M, int N, int K, const float *L, int ldl, const float *U, int ldu,
+                      const float *C, int ldc, int fp8, double *Cref, double *Sabs);
 
-/* ------------------------------------------------------------------------ */
-/* TournPivot over active rows [k, m) and panel columns [k, k+w) (Section     */
-/* 7.3).  win receives w row positions (w <= m-k) in the root's pivot order.  */
-/* Returns 0, or -1 on bad arguments.                                         */
-/* ------------------------------------------------------------------------ */
-int oracle_tslu_select(int m, int lda, const double *A, int k, int w, int h, int *win)
-{
-    int nact = m - k;
-    if (w <= 0 || h <= 0 || nact < w)
-        return -1;
-    int nleaf = (nact + h - 1) / h;
-    int cap = (h > 2 * w ? h : 2 * w);
-    int *cur = (int *)malloc((size_t)nleaf * cap * sizeof(int));
-    int *nxt = (int *)malloc((size_t)nleaf * cap * sizeof(int));
-    int *ncur = (int *)malloc((size_t)nleaf * sizeof(int));
-    int *nnxt = (int *)malloc((size_t)nleaf * sizeof(int));
+#define REAL double
+#define FMA fma
+#define FABS fabs
+#define FN(name) name
+#include "lu_oracle_body.h"
+#undef REAL
+#undef FMA
+#undef FABS
+#undef FN
 
-    /* leaves: local LUP on h consecutive rows */
-#pragma omp parallel for schedule(dynamic)
-    for (int f = 0; f < nleaf; ++f) {
-        int r0 = k + f * h;
-        int nr = (r0 + h <= m) ? h : (m - r0);
-        int *rows = (int *)malloc((size_t)nr * sizeof(int));
-        for (int i = 0; i < nr; ++i)
-            rows[i] = r0 + i;
-        gepp_select(A, lda, k, w, rows, nr, &cur[(size_t)f * cap]);
-        ncur[f] = nr < w ? nr : w;
-        free(rows);
-    }
-    /* playoff rounds: pair (0,1), (2,3), ...; an odd last node goes up */
-    int nnode = nleaf;
-    while (nnode > 1) {
-        int npar = (nnode + 1) / 2;
-#pragma omp parallel for schedule(dynamic)
-        for (int p = 0; p < npar; ++p) {
-            int l = 2 * p, r = 2 * p + 1;
-            int *dst = &nxt[(size_t)p * cap];
-            if (r >= nnode) {
-                memcpy(dst, &cur[(size_t)l * cap], (size_t)ncur[l] * sizeof(int));
-                nnxt[p] = ncur[l];
-            } else {
-                int ns = ncur[l] + ncur[r];
-                int *stack = (int *)malloc((size_t)ns * sizeof(int));
-                memcpy(stack, &cur[(size_t)l * cap], (size_t)ncur[l] * sizeof(int));
-                memcpy(stack + ncur[l], &cur[(size_t)r * cap], (size_t)ncur[r] * sizeof(int));
-                gepp_select(A, lda, k, w, stack, ns, dst);
-                nnxt[p] = ns < w ? ns : w;
-                free(stack);
-            }
-        }
-        int *t = cur; cur = nxt; nxt = t;
-        int *tn = ncur; ncur = nnxt; nnxt = tn;
-        nnode = npar;
-    }
-    /* A single leaf is its own root: its selection is already in pivot order. */
-    memcpy(win, cur, (size_t)w * sizeof(int));
-    free(cur);
-    free(nxt);
-    free(ncur);
-    free(nnxt);
-    return 0;
-}
-
-/* ------------------------------------------------------------------------ */
-/* Blocked right-looking LU with tournament pivoting (Algorithm 1 on one      */
-/* node).  A is m x n row-major (lda >= n).  piv has min(m,n) entries:        */
-/* piv[i] = the 0-based row swapped with row i at step i (LAPACK ipiv,        */
-/* 0-based).  info = 0, or j+1 for the first j with U(j,j) == 0.              */
-/* cnt may be NULL.  nthreads > 1 parallelises independent row loops only;   */
-/* each element's operation sequence is the same for every thread count.    */
-/* Returns 0, or a negative argument index on bad arguments.                  */
-/* ------------------------------------------------------------------------ */
-int oracle_lu_factor(int m, int n, double *A, int lda, int b, int h,
-                     int *piv, int *info, oracle_counts *cnt)
-{
-    if (m < 0) return -1;
-    if (n < 0) return -2;
-    if (lda < (n > 1 ? n : 1)) return -4;
-    if (b < 1) return -5;
-    if (h < 1) return -6;
-    int kmax = m < n ? m : n;
-    long long c_div = 0, c_fma = 0;
-    *info = 0;
-    int *win = (int *)malloc((size_t)(b > 0 ? b : 1) * sizeof(int));
-    for (int k = 0; k < kmax; k += b) {
-        int w = (kmax - k) < b ? (kmax - k) : b;
-
-        /* 1. TournPivot on the current values of the panel */
-        oracle_tslu_select(m, lda, A, k, w, h, win);
-
-        /* 2. sequential swaps: winner j goes to row k+j; track where the
-         *    rows of the top block move so later winners are found */
-        for (int j = 0; j < w; ++j) {
-            int p = win[j];
-            /* a winner that sat in a top row already moved may have moved */
-            for (int jj = 0; jj < j; ++jj)
-                if (p == k + jj)
-                    p = piv[k + jj];
-            piv[k + j] = p;
-            if (p != k + j) {
-                double *ra = &IDX(A, lda, k + j, 0), *rb = &IDX(A, lda, p, 0);
-                for (int c = 0; c < n; ++c) {
-                    double t = ra[c];
-                    ra[c] = rb[c];
-                    rb[c] = t;
-                }
-            }
-        }
-
-        /* 3. A00: no-pivot LU of the w x w block */
-        for (int j = 0; j < w; ++j) {
-            double u = IDX(A, lda, k + j, k + j);
-            if (u == 0.0 && *info == 0)
-                *info = k + j + 1;
-            for (int i = j + 1; i < w; ++i) {
-                double l;
-                if (u != 0.0) {
-                    l = IDX(A, lda, k + i, k + j) / u;
-                    ++c_div;
-                } else {
-                    l = 0.0;
-                }
-                IDX(A, lda, k + i, k + j) = l;
-                for (int c = j + 1; c < w; ++c) {
-                    IDX(A, lda, k + i, k + c) =
-                        fma(-l, IDX(A, lda, k + j, k + c), IDX(A, lda, k + i, k + c));
-                    ++c_fma;
-                }
-            }
-        }
-
-        /* 4. L21 = A21 * U00^{-1}: column by column, forward */
-        long long fma_l21 = 0, div_l21 = 0;
-#pragma omp parallel for schedule(static) reduction(+ : fma_l21, div_l21)
-        for (int i = k + w; i < m; ++i) {
-            double *row = &IDX(A, lda, i, 0);
-            for (int j = 0; j < w; ++j) {
-                double a = row[k + j];
-                for (int p = 0; p < j; ++p) {
-                    a = fma(-row[k + p], IDX(A, lda, k + p, k + j), a);
-                    ++fma_l21;
-                }
-                double u = IDX(A, lda, k + j, k + j);
-                if (u != 0.0) {
-                    row[k + j] = a / u;
-                    ++div_l21;
-                } else {
-                    row[k + j] = 0.0;
-                }
-            }
-        }
-        c_fma += fma_l21;
-        c_div += div_l21;
-
-        /* 5. U12 = L00^{-1} * A12: row by row, forward */
-        for (int i = 1; i < w; ++i) {
-            double *row = &IDX(A, lda, k + i, 0);
-            for (int p = 0; p < i; ++p) {
-                double l = row[k + p];
-                const double *up = &IDX(A, lda, k + p, 0);
-                for (int c = k + w; c < n; ++c) {
-                    row[c] = fma(-l, up[c], row[c]);
-                    ++c_fma;
-                }
-            }
-        }
-
-        /* 6. A22 -= L21 * U12: for each element, p ascending */
-        long long fma_s = 0;
-#pragma omp parallel for schedule(static) reduction(+ : fma_s)
-        for (int i = k + w; i < m; ++i) {
-            double *row = &IDX(A, lda, i, 0);
-            for (int p = 0; p < w; ++p) {
-                double l = row[k + p];
-                const double *up = &IDX(A, lda, k + p, 0);
-                for (int c = k + w; c < n; ++c)
-                    row[c] = fma(-l, up[c], row[c]);
-                fma_s += (n - k - w) > 0 ? (n - k - w) : 0;
-            }
-        }
-        c_fma += fma_s;
-    }
-    free(win);
-    if (cnt) {
-        cnt->s1_div = c_div;
-        cnt->s2_fma = c_fma;
-    }
-    return 0;
-}
-
-/* ------------------------------------------------------------------------ */
-/* Solve A X = B with the factors of oracle_lu_factor (n x n):               */
-/* X = U^{-1} L^{-1} P B.  B is n x nrhs row-major (ldb >= nrhs), overwritten.*/
-/* ------------------------------------------------------------------------ */
-int oracle_lu_solve(int n, int nrhs, const double *LU, int lda, const int *piv,
-                    double *B, int ldb)
-{
-    if (n < 0) return -1;
-    if (nrhs < 0) return -2;
-    if (lda < (n > 1 ? n : 1)) return -4;
-    if (ldb < (nrhs > 1 ? nrhs : 1)) return -7;
-    for (int i = 0; i < n; ++i) {
-        int p = piv[i];
-        if (p != i)
-            for (int c = 0; c < nrhs; ++c) {
-                double t = IDX(B, ldb, i, c);
-                IDX(B, ldb, i, c) = IDX(B, ldb, p, c);
-                IDX(B, ldb, p, c) = t;
-            }
-    }
-    for (int i = 0; i < n; ++i)
-        for (int p = 0; p < i; ++p) {
-            double l = IDX(LU, lda, i, p);
-            for (int c = 0; c < nrhs; ++c)
-                IDX(B, ldb, i, c) = fma(-l, IDX(B, ldb, p, c), IDX(B, ldb, i, c));
-        }
-    for (int i = n - 1; i >= 0; --i) {
-        for (int p = i + 1; p < n; ++p) {
-            double u = IDX(LU, lda, i, p);
-            for (int c = 0; c < nrhs; ++c)
-                IDX(B, ldb, i, c) = fma(-u, IDX(B, ldb, p, c), IDX(B, ldb, i, c));
-        }
-        double d = IDX(LU, lda, i, i);
-        for (int c = 0; c < nrhs; ++c)
-            IDX(B, ldb, i, c) = IDX(B, ldb, i, c) / d;
-    }
-    return 0;
-}
+#define REAL float
+#define FMA fmaf
+#define FABS fabsf
+#define FN(name) name##_f32
+#include "lu_oracle_body.h"
+#undef REAL
+#undef FMA
+#undef FABS
+#undef FN
 
 /* ------------------------------------------------------------------------ */
 /* Relative backward error per right-hand side (FP64):                       */
@@ -388,4 +129,125 @@ int oracle_set_threads(int nthreads)
     (void)nthreads;
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Low-precision operands of the mixed-precision Schur update (the paper is */
+/* silent on precision).  Written from the format definitions:              */
+/*   bfloat16: the upper 16 bits of binary32, round to nearest, ties even.  */
+/*   fp8 e4m3 (OCP): 4 exponent bits (bias 7), 3 fraction bits, subnormal   */
+/*   spacing 2^-9, largest finite 448; round to nearest, ties even, and     */
+/*   saturate to +-448.                                                      */
+/* ------------------------------------------------------------------------ */
+float oracle_round_bf16(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u)
+        return x;
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    u &= 0xFFFF0000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+float oracle_round_e4m3(float x)
+{
+    if (x != x)
+        return x;
+    double a = fabs((double)x);
+    if (a == 0.0)
+        return x;
+    int e;
+    frexp(a, &e);            /* a in [2^(e-1), 2^e) */
+    int k = e - 1;
+    if (k < -6)
+        k = -6;              /* subnormal range: fixed spacing 2^-9 */
+    double q = ldexp(1.0, k - 3);
+    double r = rint(a / q) * q;
+    if (r > 448.0)
+        r = 448.0;
+    return (float)(x < 0 ? -r : r);
+}
+
+/* Smallest e with maxabs * 2^-e <= 448, decided in binary32 (v = maxabs/448
+ * rounded to float), the precision the GPU decides it in. */
+int oracle_e4m3_exponent(float maxabs)
+{
+    if (!(maxabs > 0.0f) || isinf(maxabs))
+        return 0;
+    float v = maxabs / 448.0f;
+    int e;
+    float f = frexpf(v, &e);
+    return (f == 0.5f) ? e - 1 : e;
+}
+
+/* Reference of the scaled low-precision update, one 256 x 256 scale tile per
+ * operand block:
+ *   Cref[i][j] = C[i][j] - 2^(eL(i/256) + eU(j/256)) * sum_p qL[i][p] qU[p][j]
+ * with qL = round(L * 2^-eL), qU = round(U * 2^-eU), sums in binary64, and
+ * Sabs[i][j] = 2^(eL+eU) * sum_p |qL qU| (for error bounds).  fp8 = 0: bf16
+ * operands, e = 0. */
+void oracle_gemm_lowp(int M, int N, int K, const float *L, int ldl, const float *U, int ldu,
+                      const float *C, int ldc, int fp8, double *Cref, double *Sabs)
+{
+    int nbm = (M + 255) / 256, nbn = (N + 255) / 256;
+    int *eL = (int *)calloc((size_t)nbm + 1, sizeof(int));
+    int *eU = (int *)calloc((size_t)nbn + 1, sizeof(int));
+    if (fp8) {
+        for (int b = 0; b < nbm; ++b) {
+            float mx = 0.0f;
+            for (int i = b * 256; i < M && i < b * 256 + 256; ++i)
+                for (int p = 0; p < K; ++p)
+                    if (fabsf(L[(size_t)i * ldl + p]) > mx)
+                        mx = fabsf(L[(size_t)i * ldl + p]);
+            eL[b] = oracle_e4m3_exponent(mx);
+        }
+        for (int b = 0; b < nbn; ++b) {
+            float mx = 0.0f;
+            for (int p = 0; p < K; ++p)
+                for (int j = b * 256; j < N && j < b * 256 + 256; ++j)
+                    if (fabsf(U[(size_t)p * ldu + j]) > mx)
+                        mx = fabsf(U[(size_t)p * ldu + j]);
+            eU[b] = oracle_e4m3_exponent(mx);
+        }
+    }
+    double *qL = (double *)malloc((size_t)M * (K > 0 ? K : 1) * sizeof(double));
+    double *qU = (double *)malloc((size_t)(K > 0 ? K : 1) * N * sizeof(double));
+    for (int i = 0; i < M; ++i)
+        for (int p = 0; p < K; ++p) {
+            float x = ldexpf(L[(size_t)i * ldl + p], -eL[i / 256]);
+            qL[(size_t)i * K + p] = fp8 ? oracle_round_e4m3(x) : oracle_round_bf16(x);
+        }
+    for (int p = 0; p < K; ++p)
+        for (int j = 0; j < N; ++j) {
+            float x = ldexpf(U[(size_t)p * ldu + j], -eU[j / 256]);
+            qU[(size_t)p * N + j] = fp8 ? oracle_round_e4m3(x) : oracle_round_bf16(x);
+        }
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < N; ++j) {
+            double s = 0.0, sa = 0.0;
+            for (int p = 0; p < K; ++p) {
+                double t = qL[(size_t)i * K + p] * qU[(size_t)p * N + j];
+                s += t;
+                sa += fabs(t);
+            }
+            int e = eL[i / 256] + eU[j / 256];
+            Cref[(size_t)i * N + j] = (double)C[(size_t)i * ldc + j] - ldexp(s, e);
+            Sabs[(size_t)i * N + j] = ldexp(sa, e);
+        }
+    free(qL);
+    free(qU);
+    free(eL);
+    free(eU);
+}
+
+/* Elementwise roundings of an array (test access to the two quantizers). */
+void oracle_round_array(const float *x, float *y, long long n, int fp8)
+{
+    for (long long i = 0; i < n; ++i)
+        y[i] = fp8 ? oracle_round_e4m3(x[i]) : oracle_round_bf16(x[i]);
 }

@@ -15,6 +15,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lu_oracle.c")
+_DEPS = [_SRC, os.path.join(_HERE, "lu_oracle_body.h")]
 _lock = threading.Lock()
 _lib = None
 
@@ -27,7 +28,7 @@ def build(force: bool = False) -> str:
     """Compile lu_oracle.c with gcc (-ffp-contract=off keeps every fused
     operation explicit).  Returns the shared-library path."""
     out = lib_path()
-    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+    if not force and os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(d) for d in _DEPS):
         return out
     os.makedirs(os.path.dirname(out), exist_ok=True)
     tmp = out + f".tmp{os.getpid()}"
@@ -59,6 +60,18 @@ def _load():
             lib.oracle_backward_error.restype = None
             lib.oracle_set_threads.argtypes = [I]
             lib.oracle_set_threads.restype = I
+            lib.oracle_lu_factor_f32.argtypes = [I, I, P, I, I, I, P, P, P]
+            lib.oracle_lu_factor_f32.restype = I
+            lib.oracle_lu_factor_q_f32.argtypes = [I, I, P, I, I, I, P, P, P, I]
+            lib.oracle_lu_factor_q_f32.restype = I
+            lib.oracle_lu_solve_f32.argtypes = [I, I, P, I, P, P, I]
+            lib.oracle_lu_solve_f32.restype = I
+            lib.oracle_gemm_lowp.argtypes = [I, I, I, P, I, P, I, P, I, I, P, P]
+            lib.oracle_gemm_lowp.restype = None
+            lib.oracle_round_array.argtypes = [P, P, ctypes.c_longlong, I]
+            lib.oracle_round_array.restype = None
+            lib.oracle_e4m3_exponent.argtypes = [ctypes.c_float]
+            lib.oracle_e4m3_exponent.restype = I
             _lib = lib
     return _lib
 
@@ -133,3 +146,62 @@ def backward_error(A: np.ndarray, B: np.ndarray, X: np.ndarray) -> np.ndarray:
     lib.oracle_backward_error(n, nrhs, _ptr(A), max(n, 1), _ptr(Bm), max(nrhs, 1),
                               _ptr(Xm), max(nrhs, 1), _ptr(eta))
     return eta
+
+
+def lu_factor_f32(A: np.ndarray, b: int, h: int = 128, lowp: int = 0):
+    """binary32 instance of the same tournament LU (fmaf, IEEE float division).
+    lowp = 1 / 2: the Schur update takes bfloat16 / fp8-e4m3 operands with
+    per-256-block power-of-two scales (the mixed-precision factorization)."""
+    lib = _load()
+    LU = np.ascontiguousarray(A, dtype=np.float32).copy()
+    m, n = LU.shape
+    piv = np.zeros(max(min(m, n), 1), dtype=np.int32)
+    info = ctypes.c_int(0)
+    cnt = _Counts()
+    rc = lib.oracle_lu_factor_q_f32(m, n, _ptr(LU), max(n, 1), int(b), int(h), _ptr(piv),
+                                    ctypes.byref(info), ctypes.byref(cnt), int(lowp))
+    if rc != 0:
+        raise ValueError(f"oracle_lu_factor_f32: argument {-rc} invalid")
+    return LU, piv[: min(m, n)], info.value
+
+
+def lu_solve_f32(LU: np.ndarray, piv: np.ndarray, B: np.ndarray) -> np.ndarray:
+    lib = _load()
+    LU = np.ascontiguousarray(LU, dtype=np.float32)
+    n = LU.shape[0]
+    vec = B.ndim == 1
+    X = np.ascontiguousarray(B.reshape(n, -1), dtype=np.float32).copy()
+    nrhs = X.shape[1]
+    piv = np.ascontiguousarray(piv, dtype=np.int32)
+    lib.oracle_lu_solve_f32(n, nrhs, _ptr(LU), max(n, 1), _ptr(piv), _ptr(X), max(nrhs, 1))
+    return X[:, 0] if vec else X
+
+
+def round_lowp(x: np.ndarray, fp8: bool) -> np.ndarray:
+    """bfloat16 (fp8=False) or fp8 e4m3 with saturation (fp8=True), as float32."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty_like(x)
+    lib.oracle_round_array(_ptr(x), _ptr(y), x.size, 1 if fp8 else 0)
+    return y
+
+
+def e4m3_exponent(maxabs: float) -> int:
+    return _load().oracle_e4m3_exponent(float(maxabs))
+
+
+def gemm_lowp(L: np.ndarray, U: np.ndarray, C: np.ndarray, fp8: bool):
+    """Reference of C - s * q(L) q(U) with per-256-block power-of-two scales.
+    Returns (Cref, Sabs) in float64 (Sabs = s * sum |qL qU|)."""
+    lib = _load()
+    L = np.ascontiguousarray(L, dtype=np.float32)
+    U = np.ascontiguousarray(U, dtype=np.float32)
+    C = np.ascontiguousarray(C, dtype=np.float32)
+    M, K = L.shape
+    K2, N = U.shape
+    assert K == K2 and C.shape == (M, N)
+    Cref = np.empty((M, N), dtype=np.float64)
+    Sabs = np.empty((M, N), dtype=np.float64)
+    lib.oracle_gemm_lowp(M, N, K, _ptr(L), max(K, 1), _ptr(U), max(N, 1), _ptr(C), max(N, 1),
+                         1 if fp8 else 0, _ptr(Cref), _ptr(Sabs))
+    return Cref, Sabs

@@ -27,6 +27,11 @@ from .api import (  # noqa: F401
     lu_factor_ex,
     lu_solve,
     lu_factor_host,
+    lu_factor_f32,
+    lu_solve_f32,
+    lu_gemm_lowp,
+    lu_residual,
+    ir_solve,
     prof_begin,
     prof_end,
     kernel_launch_count,

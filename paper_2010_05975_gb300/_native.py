@@ -35,6 +35,17 @@ class lu_opts(ctypes.Structure):
                 ("reserved", ctypes.c_int * 5)]
 
 
+class ir_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("b", ctypes.c_int), ("h", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+class ir_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("gmres_iters", ctypes.c_int), ("path", ctypes.c_int),
+                ("info", ctypes.c_int), ("eta", ctypes.c_double), ("eta0", ctypes.c_double),
+                ("precision", ctypes.c_int), ("refactors", ctypes.c_int)]
+
+
 class lu_prof_entry(ctypes.Structure):
     _fields_ = [("kernel_class", ctypes.c_int), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double),
                 ("total_flops", ctypes.c_double), ("total_bytes", ctypes.c_double)]
@@ -53,6 +64,11 @@ _SIGS = {
     "lu_factor": ([I, P, I, P, P, P], I),
     "lu_factor_ex": ([I, I, P, I, P, P, ctypes.POINTER(lu_opts), P], I),
     "lu_solve": ([I, I, P, I, P, P, I, P], I),
+    "lu_factor_f32": ([I, I, P, I, P, P, ctypes.POINTER(lu_opts), P], I),
+    "lu_solve_f32": ([I, I, P, I, P, P, I, P], I),
+    "lu_gemm_lowp": ([I, I, I, P, I, P, I, P, I, I, P, P], I),
+    "lu_residual": ([I, I, P, I, P, I, P, I, P, I, P, P], I),
+    "ir_solve": ([I, I, P, I, P, I, P, I, ctypes.POINTER(ir_opts), ctypes.POINTER(ir_result), P], I),
     "lu_prof_begin": ([], I),
     "lu_prof_end": ([P, I, P], I),
     "lu_kernel_launch_count": ([], ctypes.c_ulonglong),

@@ -121,3 +121,89 @@ def lu_factor_host(A_host: torch.Tensor, b: int = 0, h: int = 0, out: torch.Tens
         info_h.copy_(info, non_blocking=True)
     s.synchronize()
     return out, piv_h, int(info_h[0])
+
+
+def lu_factor_f32(A: torch.Tensor, b: int = 0, h: int = 0, precision: int = nat.LU_PREC_F32,
+                  piv: torch.Tensor | None = None, info: torch.Tensor | None = None, stream=None):
+    """In-place factorization of a float32 CUDA matrix.  precision selects the
+    Schur-update operands: F32, BF16 or FP8 (tensor cores)."""
+    _require(A, "A", torch.float32, 2)
+    m, n = A.shape
+    k = min(m, n)
+    if piv is None:
+        piv = torch.empty(max(k, 1), dtype=torch.int32, device=A.device)
+    if info is None:
+        info = torch.empty(1, dtype=torch.int32, device=A.device)
+    opts = nat.lu_opts(b, h, precision)
+    rc = nat.library().lu_factor_f32(m, n, A.data_ptr(), max(A.stride(0), 1), piv.data_ptr(), info.data_ptr(),
+                                     ctypes.byref(opts), _stream_handle(stream))
+    nat.check("lu_factor_f32", rc)
+    return piv[:k], info
+
+
+def lu_solve_f32(LU: torch.Tensor, piv: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
+    _require(LU, "LU", torch.float32, 2)
+    n = LU.shape[0]
+    B2 = B if B.dim() == 2 else B.view(n, 1)
+    _require(B2, "B", torch.float32, 2)
+    rc = nat.library().lu_solve_f32(n, B2.shape[1], LU.data_ptr(), max(LU.stride(0), 1), piv.data_ptr(),
+                                    B2.data_ptr(), max(B2.stride(0), 1), _stream_handle(stream))
+    nat.check("lu_solve_f32", rc)
+    return B
+
+
+def lu_gemm_lowp(L: torch.Tensor, U: torch.Tensor, C: torch.Tensor, precision: int = nat.LU_PREC_BF16,
+                 status: torch.Tensor | None = None, stream=None):
+    """C -= sL sU round(L/sL) round(U/sU) on the tensor cores (float32 in/out)."""
+    for t, nm in ((L, "L"), (U, "U"), (C, "C")):
+        _require(t, nm, torch.float32, 2)
+    M, K = L.shape
+    N = U.shape[1]
+    if status is None:
+        status = torch.empty(1, dtype=torch.int32, device=C.device)
+    rc = nat.library().lu_gemm_lowp(M, N, K, L.data_ptr(), max(L.stride(0), 1), U.data_ptr(), max(U.stride(0), 1),
+                                    C.data_ptr(), max(C.stride(0), 1), precision, status.data_ptr(),
+                                    _stream_handle(stream))
+    nat.check("lu_gemm_lowp", rc)
+    return C, status
+
+
+def lu_residual(A: torch.Tensor, X: torch.Tensor, B: torch.Tensor, R: torch.Tensor | None = None,
+                eta: torch.Tensor | None = None, stream=None):
+    """R = B - A X (float64) and eta per column."""
+    _require(A, "A", torch.float64, 2)
+    n = A.shape[0]
+    X2 = X if X.dim() == 2 else X.view(n, 1)
+    B2 = B if B.dim() == 2 else B.view(n, 1)
+    nr = X2.shape[1]
+    if R is None:
+        R = torch.empty((n, nr), dtype=torch.float64, device=A.device)
+    if eta is None:
+        eta = torch.empty(nr, dtype=torch.float64, device=A.device)
+    rc = nat.library().lu_residual(n, nr, A.data_ptr(), max(A.stride(0), 1), X2.data_ptr(), max(X2.stride(0), 1),
+                                   B2.data_ptr(), max(B2.stride(0), 1), R.data_ptr(), max(R.stride(0), 1),
+                                   eta.data_ptr(), _stream_handle(stream))
+    nat.check("lu_residual", rc)
+    return R, eta
+
+
+def ir_solve(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor | None = None, precision: int = nat.LU_PREC_BF16,
+             tol: float = 1e-12, b: int = 0, h: int = 0, max_iter: int = 0, gmres_restart: int = 0, stream=None):
+    """Solve A X = B (float64 CUDA tensors) with a low-precision factorization
+    and float64 refinement.  Synchronizes the stream; returns (X, result)."""
+    _require(A, "A", torch.float64, 2)
+    n = A.shape[0]
+    B2 = B if B.dim() == 2 else B.view(n, 1)
+    _require(B2, "B", torch.float64, 2)
+    if X is None:
+        X = torch.empty_like(B2)
+    X2 = X if X.dim() == 2 else X.view(n, 1)
+    opts = nat.ir_opts(precision, b, h, tol, max_iter, gmres_restart)
+    res = nat.ir_result()
+    rc = nat.library().ir_solve(n, B2.shape[1], A.data_ptr(), max(A.stride(0), 1), B2.data_ptr(),
+                                max(B2.stride(0), 1), X2.data_ptr(), max(X2.stride(0), 1), ctypes.byref(opts),
+                                ctypes.byref(res), _stream_handle(stream))
+    nat.check("ir_solve", rc)
+    out = {"iters": res.iters, "gmres_iters": res.gmres_iters, "path": res.path, "info": res.info,
+           "eta": res.eta, "eta0": res.eta0, "precision": res.precision, "refactors": res.refactors}
+    return X, out

@@ -8,7 +8,7 @@ namespace lu {
 struct FactorWs {
     int* lists = nullptr;
     int* counts = nullptr;
-    double* a00 = nullptr;
+    void* a00 = nullptr;
     int* mv = nullptr;
     size_t stride_nodes = 0;
 };
@@ -21,11 +21,11 @@ static void ws_free(FactorWs& ws, cudaStream_t s) {
     ws = FactorWs{};
 }
 
-static int ws_alloc(FactorWs& ws, int m, int b, int h, cudaStream_t s) {
+static int ws_alloc(FactorWs& ws, int m, int b, int h, size_t elem, cudaStream_t s) {
     ws.stride_nodes = static_cast<size_t>(cdiv(m, h > 0 ? h : 1)) + 1;
     bool ok = cudaMallocAsync(reinterpret_cast<void**>(&ws.lists), 2 * ws.stride_nodes * b * sizeof(int), s) == cudaSuccess &&
               cudaMallocAsync(reinterpret_cast<void**>(&ws.counts), 2 * ws.stride_nodes * sizeof(int), s) == cudaSuccess &&
-              cudaMallocAsync(reinterpret_cast<void**>(&ws.a00), static_cast<size_t>(b) * b * sizeof(double), s) == cudaSuccess &&
+              cudaMallocAsync(&ws.a00, static_cast<size_t>(b) * b * elem, s) == cudaSuccess &&
               cudaMallocAsync(reinterpret_cast<void**>(&ws.mv), (1 + 4 * static_cast<size_t>(b)) * sizeof(int), s) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -39,13 +39,25 @@ static int ws_alloc(FactorWs& ws, int m, int b, int h, cudaStream_t s) {
 // uses ~1 KB of static shared memory).
 constexpr size_t kTsluSmemLimit = 232448 - 2048;
 
-static bool tslu_shapes_fit(int m, int kmax, int b, int h) {
+static bool tslu_shapes_fit(int m, int kmax, int b, int h, int elem) {
     for (int k = 0; k < kmax; k += b) {
         const int w = (kmax - k) < b ? (kmax - k) : b;
-        if (tslu_shape(m, k, w, h, kTsluMaxCluster).smem > kTsluSmemLimit) return false;
+        if (tslu_shape(m, k, w, h, kTsluMaxCluster, elem).smem > kTsluSmemLimit) return false;
     }
     return true;
 }
+
+// Schur update of columns [c0, c1) for one step, by arithmetic.
+struct SchurF64 {
+    int operator()(double* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s) const {
+        return schur_f64(A, lda, m, k, w, c0, c1, s);
+    }
+};
+struct SchurF32 {
+    int operator()(float* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s) const {
+        return schur_f32(A, lda, m, k, w, c0, c1, s);
+    }
+};
 
 // Step loop with a one-panel lookahead.  On the caller's stream s, step t
 // runs: wait for its tournament -> apply pivots -> L21, U12 -> the Schur
@@ -53,12 +65,15 @@ static bool tslu_shapes_fit(int m, int kmax, int b, int h) {
 // The next tournament reads only those panel columns, so it runs on a
 // high-priority side stream concurrently with the rest of the update; the
 // next step's pivot application waits for both.
-static int factor_f64(int m, int n, double* A, int lda, int* piv, int* info, int b, int h, cudaStream_t s) {
+template <typename T, typename Schur>
+static int factor_loop(int m, int n, T* A, int lda, int* piv, int* info, int b, int h, const Schur& schur,
+                       cudaStream_t s) {
     LU_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
     const int kmax = m < n ? m : n;
     if (kmax == 0) return 0;
     FactorWs ws;
-    if (int rc = ws_alloc(ws, m, b, h, s)) return rc;
+    if (int rc = ws_alloc(ws, m, b, h, sizeof(T), s)) return rc;
+    T* a00 = static_cast<T*>(ws.a00);
     int lo = 0, hi = 0;
     cudaStream_t s2 = nullptr;
     cudaEvent_t ev_panel = nullptr, ev_tslu = nullptr;
@@ -71,28 +86,28 @@ static int factor_f64(int m, int n, double* A, int lda, int* piv, int* info, int
     const int* root = nullptr;
     if (!rc && cudaEventRecord(ev_panel, s) != cudaSuccess) rc = LU_ELAUNCH;
     if (!rc && cudaStreamWaitEvent(s2, ev_panel, 0) != cudaSuccess) rc = LU_ELAUNCH;
-    if (!rc) rc = tslu_select_f64(A, lda, m, 0, (kmax < b ? kmax : b), h, ws.lists, ws.counts, ws.stride_nodes,
-                                  ws.a00, info, &root, s2);
+    if (!rc) rc = tslu_select<T>(A, lda, m, 0, (kmax < b ? kmax : b), h, ws.lists, ws.counts, ws.stride_nodes, a00,
+                                 info, &root, s2);
     if (!rc && cudaEventRecord(ev_tslu, s2) != cudaSuccess) rc = LU_ELAUNCH;
     for (int k = 0; k < kmax && rc == 0; k += b) {
         const int w = (kmax - k) < b ? (kmax - k) : b;
         const int kn = k + w;
         const int wn = (kmax - kn) < b ? (kmax - kn) : b;     // next panel width (<= 0: none)
         if (cudaStreamWaitEvent(s, ev_tslu, 0) != cudaSuccess) { rc = LU_ELAUNCH; break; }
-        rc = pivot_apply_f64(A, lda, m, n, k, w, root, ws.a00, piv, ws.mv, s);
-        if (!rc) rc = trsm_l21_f64(A, lda, m, k, w, s);
-        if (!rc) rc = trsm_u12_f64(A, lda, n, k, w, s);
+        rc = pivot_apply<T>(A, lda, m, n, k, w, root, a00, piv, ws.mv, s);
+        if (!rc) rc = trsm_l21<T>(A, lda, m, k, w, s);
+        if (!rc) rc = trsm_u12<T>(A, lda, n, k, w, s);
         if (rc) break;
         if (wn > 0) {
-            rc = schur_f64(A, lda, m, k, w, kn, kn + wn, s);
+            rc = schur(A, lda, m, k, w, kn, kn + wn, s);
             if (!rc && cudaEventRecord(ev_panel, s) != cudaSuccess) rc = LU_ELAUNCH;
             if (!rc && cudaStreamWaitEvent(s2, ev_panel, 0) != cudaSuccess) rc = LU_ELAUNCH;
-            if (!rc) rc = tslu_select_f64(A, lda, m, kn, wn, h, ws.lists, ws.counts, ws.stride_nodes, ws.a00,
-                                          info, &root, s2);
+            if (!rc) rc = tslu_select<T>(A, lda, m, kn, wn, h, ws.lists, ws.counts, ws.stride_nodes, a00, info,
+                                         &root, s2);
             if (!rc && cudaEventRecord(ev_tslu, s2) != cudaSuccess) rc = LU_ELAUNCH;
-            if (!rc) rc = schur_f64(A, lda, m, k, w, kn + wn, n, s);
+            if (!rc) rc = schur(A, lda, m, k, w, kn + wn, n, s);
         } else {
-            rc = schur_f64(A, lda, m, k, w, kn, n, s);
+            rc = schur(A, lda, m, k, w, kn, n, s);
         }
     }
     // join the side stream before the workspace goes back to the pool
@@ -107,12 +122,10 @@ static int factor_f64(int m, int n, double* A, int lda, int* piv, int* info, int
     return rc;
 }
 
-}  // namespace lu
-
-using namespace lu;
-
-extern "C" int lu_factor_ex(int m, int n, double* A, int lda, int* piv, int* info, const lu_opts* opts,
-                            cudaStream_t stream) {
+// Shared argument checks of the factor entry points.  Returns 0 and fills
+// b, h, prec, or a negative argument index.
+static int factor_args(int m, int n, const void* A, int lda, const int* piv, const int* info, const lu_opts* opts,
+                       int elem, int& b, int& h, int& prec) {
     if (m < 0) return -1;
     if (n < 0) return -2;
     if (lda < (n > 1 ? n : 1)) return -4;
@@ -120,19 +133,128 @@ extern "C" int lu_factor_ex(int m, int n, double* A, int lda, int* piv, int* inf
     if (kmax > 0 && A == nullptr) return -3;
     if (kmax > 0 && piv == nullptr) return -5;
     if (info == nullptr) return -6;
-    int b = (n >= 4096) ? 256 : 32, h = 128, prec = LU_PREC_F64;
+    b = (n >= 4096) ? 256 : 32;
+    h = 128;
+    prec = (elem == 8) ? LU_PREC_F64 : LU_PREC_F32;
     if (opts) {
         if (opts->b < 0 || opts->h < 0) return -7;
         for (int r : opts->reserved)
             if (r != 0) return -7;
         if (opts->b > 0) b = opts->b;
         if (opts->h > 0) h = opts->h;
-        prec = opts->precision;
+        if (opts->precision != 0 || elem == 8) prec = opts->precision;
     }
     if (b > kMaxPanel) return -7;
+    if (kmax > 0 && !tslu_shapes_fit(m, kmax, b, h, elem)) return -7;
+    return 0;
+}
+
+// Schur update with bf16 / fp8 operands on the tensor cores.  L21 and all of
+// U12 are quantized once per step (the first call of the step), then each
+// column range is one tcgen05 launch.
+struct SchurLowp {
+    bool fp8;
+    int n;
+    unsigned char* Lq;
+    unsigned char* Uq;
+    int* expL;
+    int* expU;
+    int* status;
+    mutable int last_k = -1;
+    int operator()(float* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s) const {
+        const int r0 = k + w;
+        if (k != last_k) {
+            if (int rc = quantize_l21(A, lda, m, k, w, fp8, Lq, expL, s)) return rc;
+            if (int rc = quantize_u12(A, lda, k, w, r0, n, fp8, Uq, expU, s)) return rc;
+            last_k = k;
+        }
+        const size_t elem = fp8 ? 1 : 2;
+        const int off = c0 - r0;
+        return schur_tc(A + idx(r0, c0, lda), lda, m - r0, c1 - c0, Lq, Uq + static_cast<size_t>(off) * kLowpK * elem,
+                        expL, expU, 0, off, fp8, status, w, s);
+    }
+};
+
+static int factor_lowp(int m, int n, float* A, int lda, int* piv, int* info, int b, int h, int prec,
+                       cudaStream_t s) {
+    if (m != n || (b % 128) != 0) return LU_EUNSUPPORTED;
+    const bool fp8 = prec == LU_PREC_FP8;
+    const size_t elem = fp8 ? 1 : 2;
+    SchurLowp op{};
+    op.fp8 = fp8;
+    op.n = n;
+    op.status = info;
+    const size_t nblk = static_cast<size_t>(cdiv(n, 256)) + 1;
+    bool ok = cudaMallocAsync(reinterpret_cast<void**>(&op.Lq), static_cast<size_t>(m) * kLowpK * elem + 256, s) == cudaSuccess &&
+              cudaMallocAsync(reinterpret_cast<void**>(&op.Uq), static_cast<size_t>(n) * kLowpK * elem + 256, s) == cudaSuccess &&
+              cudaMallocAsync(reinterpret_cast<void**>(&op.expL), nblk * sizeof(int), s) == cudaSuccess &&
+              cudaMallocAsync(reinterpret_cast<void**>(&op.expU), nblk * sizeof(int), s) == cudaSuccess;
+    int rc = ok ? factor_loop<float>(m, n, A, lda, piv, info, b, h, op, s) : LU_ENOMEM;
+    cudaGetLastError();
+    if (op.Lq) cudaFreeAsync(op.Lq, s);
+    if (op.Uq) cudaFreeAsync(op.Uq, s);
+    if (op.expL) cudaFreeAsync(op.expL, s);
+    if (op.expU) cudaFreeAsync(op.expU, s);
+    return rc;
+}
+
+}  // namespace lu
+
+using namespace lu;
+
+extern "C" int lu_gemm_lowp(int M, int N, int K, const float* L, int ldl, const float* U, int ldu, float* C, int ldc,
+                            int precision, int* status, cudaStream_t stream) {
+    if (M < 0) return -1;
+    if (N < 0) return -2;
+    if (K < 0 || K > kLowpK) return -3;
+    if (M > 0 && K > 0 && (L == nullptr || ldl < K)) return -4;
+    if (N > 0 && K > 0 && (U == nullptr || ldu < N)) return -6;
+    if (M > 0 && N > 0 && (C == nullptr || ldc < N)) return -8;
+    if (precision != LU_PREC_BF16 && precision != LU_PREC_FP8) return -10;
+    if (status == nullptr) return -11;
+    LU_TRY(cudaMemsetAsync(status, 0, sizeof(int), stream));
+    if (M == 0 || N == 0 || K == 0) return 0;
+    const bool fp8 = precision == LU_PREC_FP8;
+    const size_t elem = fp8 ? 1 : 2;
+    unsigned char *Lq = nullptr, *Uq = nullptr;
+    int *eL = nullptr, *eU = nullptr;
+    bool ok = cudaMallocAsync(reinterpret_cast<void**>(&Lq), static_cast<size_t>(M) * kLowpK * elem + 256, stream) == cudaSuccess &&
+              cudaMallocAsync(reinterpret_cast<void**>(&Uq), static_cast<size_t>(N) * kLowpK * elem + 256, stream) == cudaSuccess &&
+              cudaMallocAsync(reinterpret_cast<void**>(&eL), (static_cast<size_t>(cdiv(M, 256)) + 1) * sizeof(int), stream) == cudaSuccess &&
+              cudaMallocAsync(reinterpret_cast<void**>(&eU), (static_cast<size_t>(cdiv(N, 256)) + 1) * sizeof(int), stream) == cudaSuccess;
+    int rc = LU_ENOMEM;
+    if (ok) {
+        // The quantizers read the operands as blocks of one matrix: L as
+        // rows [r0, r0+M) x columns [k, k+K) and U as rows [k, k+K) x columns
+        // [c0, c0+N).  Offsetting the base pointers maps L and U there with
+        // k = 0, r0 = K for L and c0 = K for U.
+        rc = quantize_l21(L - static_cast<ptrdiff_t>(K) * ldl, ldl, K + M, 0, K, fp8, Lq, eL, stream);
+        if (!rc) rc = quantize_u12(U - K, ldu, 0, K, K, K + N, fp8, Uq, eU, stream);
+        if (!rc) rc = schur_tc(C, ldc, M, N, Lq, Uq, eL, eU, 0, 0, fp8, status, K, stream);
+    }
+    cudaGetLastError();
+    if (Lq) cudaFreeAsync(Lq, stream);
+    if (Uq) cudaFreeAsync(Uq, stream);
+    if (eL) cudaFreeAsync(eL, stream);
+    if (eU) cudaFreeAsync(eU, stream);
+    return rc;
+}
+
+extern "C" int lu_factor_ex(int m, int n, double* A, int lda, int* piv, int* info, const lu_opts* opts,
+                            cudaStream_t stream) {
+    int b, h, prec;
+    if (int rc = factor_args(m, n, A, lda, piv, info, opts, 8, b, h, prec)) return rc;
     if (prec != LU_PREC_F64) return LU_EUNSUPPORTED;
-    if (kmax > 0 && !tslu_shapes_fit(m, kmax, b, h)) return -7;
-    return factor_f64(m, n, A, lda, piv, info, b, h, stream);
+    return factor_loop<double>(m, n, A, lda, piv, info, b, h, SchurF64{}, stream);
+}
+
+extern "C" int lu_factor_f32(int m, int n, float* A, int lda, int* piv, int* info, const lu_opts* opts,
+                             cudaStream_t stream) {
+    int b, h, prec;
+    if (int rc = factor_args(m, n, A, lda, piv, info, opts, 4, b, h, prec)) return rc;
+    if (prec == LU_PREC_F32) return factor_loop<float>(m, n, A, lda, piv, info, b, h, SchurF32{}, stream);
+    if (prec == LU_PREC_BF16 || prec == LU_PREC_FP8) return factor_lowp(m, n, A, lda, piv, info, b, h, prec, stream);
+    return -7;
 }
 
 extern "C" int lu_factor(int n, double* A, int lda, int* piv, int* info, cudaStream_t stream) {
@@ -154,4 +276,16 @@ extern "C" int lu_solve(int n, int nrhs, const double* LU, int lda, const int* p
     if (n > 0 && nrhs > 0 && B == nullptr) return -6;
     if (ldb < (nrhs > 1 ? nrhs : 1)) return -7;
     return getrs_f64(n, nrhs, LU, lda, piv, B, ldb, stream);
+}
+
+extern "C" int lu_solve_f32(int n, int nrhs, const float* LU, int lda, const int* piv, float* B, int ldb,
+                            cudaStream_t stream) {
+    if (n < 0) return -1;
+    if (nrhs < 0 || nrhs > 384) return -2;
+    if (n > 0 && LU == nullptr) return -3;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (n > 0 && piv == nullptr) return -5;
+    if (n > 0 && nrhs > 0 && B == nullptr) return -6;
+    if (ldb < (nrhs > 1 ? nrhs : 1)) return -7;
+    return getrs_f32(n, nrhs, LU, lda, piv, B, ldb, stream);
 }

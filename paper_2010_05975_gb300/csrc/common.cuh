@@ -44,21 +44,32 @@ struct TsluShape {
 // upward until a node holds more than w rows: selection is independent of
 // the order in which candidate rows are stacked, so a node made only of
 // such leaves selects from its whole contiguous row range.
-TsluShape tslu_shape(int m, int k, int w, int h, int max_cluster);
+TsluShape tslu_shape(int m, int k, int w, int h, int max_cluster, int elem);
 int tslu_max_cluster();
 
-// Host entry points of the FP64 pieces (stream-ordered, no sync).
-int tslu_select_f64(const double* A, int lda, int m, int k, int w, int h,
-                    int* lists, int* counts, size_t list_stride_nodes,
-                    double* a00, int* info, const int** root_list, cudaStream_t s);
-int pivot_apply_f64(double* A, int lda, int m, int n, int k, int w,
-                    const int* root_list, const double* a00, int* piv,
-                    int* mv, cudaStream_t s);
-int trsm_l21_f64(double* A, int lda, int m, int k, int w, cudaStream_t s);
-int trsm_u12_f64(double* A, int lda, int n, int k, int w, cudaStream_t s);
+// Host entry points of the factorization pieces (stream-ordered, no sync).
+template <typename T>
+int tslu_select(const T* A, int lda, int m, int k, int w, int h, int* lists, int* counts, size_t list_stride_nodes,
+                T* a00, int* info, const int** root_list, cudaStream_t s);
+template <typename T>
+int pivot_apply(T* A, int lda, int m, int n, int k, int w, const int* root_list, const T* a00, int* piv, int* mv,
+                cudaStream_t s);
+template <typename T>
+int trsm_l21(T* A, int lda, int m, int k, int w, cudaStream_t s);
+template <typename T>
+int trsm_u12(T* A, int lda, int n, int k, int w, cudaStream_t s);
 // A[r0:m, c0:c1) -= A[r0:m, k:k+w) * A[k:k+w, c0:c1)   (r0 = k + w)
 int schur_f64(double* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s);
-int getrs_f64(int n, int nrhs, const double* LU, int lda, const int* piv,
-              double* B, int ldb, cudaStream_t s);
+int schur_f32(float* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s);
+int getrs_f64(int n, int nrhs, const double* LU, int lda, const int* piv, double* B, int ldb, cudaStream_t s);
+int getrs_f32(int n, int nrhs, const float* LU, int lda, const int* piv, float* B, int ldb, cudaStream_t s);
+
+// Low-precision tensor-core Schur update (csrc/schur_lowp.cu).
+constexpr int kLowpK = 256;     // operand K is padded to this
+size_t lowp_smem_bytes(bool fp8);
+int quantize_l21(const float* A, int lda, int m, int k, int w, bool fp8, void* Lq, int* expL, cudaStream_t s);
+int quantize_u12(const float* A, int lda, int k, int w, int c0, int c1, bool fp8, void* Uq, int* expU, cudaStream_t s);
+int schur_tc(float* C, int ldc, int M, int N, const void* Lq, const void* Uq, const int* expL, const int* expU,
+             int row_base, int col_base, bool fp8, int* status, int w, cudaStream_t s);
 
 }  // namespace lu

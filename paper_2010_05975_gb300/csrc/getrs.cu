@@ -214,3 +214,22 @@ int getrs_f64(int n, int nrhs, const double* LU, int lda, const int* piv, double
 }
 
 }  // namespace lu
+
+namespace lu {
+int getrs_f32(int n, int nrhs, const float* LU, int lda, const int* piv, float* B, int ldb, cudaStream_t s) {
+    if (n == 0 || nrhs == 0) return 0;
+    int* perm = nullptr;
+    float* Y = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&perm), sizeof(int) * static_cast<size_t>(n), s) != cudaSuccess)
+        return LU_ENOMEM;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&Y), sizeof(float) * static_cast<size_t>(n) * nrhs, s) !=
+        cudaSuccess) {
+        cudaFreeAsync(perm, s);
+        return LU_ENOMEM;
+    }
+    int rc = getrs_impl<float>(n, nrhs, LU, lda, piv, B, ldb, perm, Y, s);
+    cudaFreeAsync(Y, s);
+    cudaFreeAsync(perm, s);
+    return rc;
+}
+}  // namespace lu

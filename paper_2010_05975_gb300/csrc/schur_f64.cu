@@ -12,49 +12,49 @@
 
 namespace lu {
 
-template <int BM, int BN>
-__global__ void __launch_bounds__(256) schur_f64_kernel(double* __restrict__ A, int lda, int m, int k, int w, int c0,
-                                                        int n) {
+template <typename T, int BM, int BN>
+__global__ void __launch_bounds__(256) schur_simt_kernel(T* __restrict__ A, int lda, int m, int k, int w, int c0,
+                                                         int n) {
     constexpr int BK = 8;
     constexpr int TM = BM / 16, TN = BN / 16;
     constexpr int APT = BM * BK / 256;          // A elements loaded per thread per chunk
     constexpr int BPT = BN * BK / 256;          // B elements loaded per thread per chunk
     constexpr int BTPR = BN / BPT;              // threads per B row
-    __shared__ double As[2][BK][BM];
-    __shared__ double Bs[2][BK][BN];
+    __shared__ T As[2][BK][BM];
+    __shared__ T Bs[2][BK][BN];
 
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     const int row0 = k + w + blockIdx.y * BM;
     const int col0 = c0 + blockIdx.x * BN;
 
-    double acc[TM][TN];
+    T acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
             const int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
-            acc[i][j] = (r < m && c < n) ? A[idx(r, c, lda)] : 0.0;
+            acc[i][j] = (r < m && c < n) ? A[idx(r, c, lda)] : T(0);
         }
 
     // loader coordinates
     const int a_r = tid % BM, a_k = (tid / BM) * APT;
     const int b_k = tid / BTPR, b_c = (tid % BTPR) * BPT;
     const bool a_row_ok = (row0 + a_r) < m;
-    const double* a_src = A + idx(row0 + a_r < m ? row0 + a_r : row0, k, lda);
-    const double* b_src = A + idx(k, col0 + b_c, lda);
+    const T* a_src = A + idx(row0 + a_r < m ? row0 + a_r : row0, k, lda);
+    const T* b_src = A + idx(k, col0 + b_c, lda);
 
-    double ra[APT], rb[BPT];
+    T ra[APT], rb[BPT];
     auto load_chunk = [&](int kc) {
 #pragma unroll
         for (int e = 0; e < APT; ++e) {
             const int kk = kc + a_k + e;
-            ra[e] = (a_row_ok && kk < w) ? a_src[kk] : 0.0;
+            ra[e] = (a_row_ok && kk < w) ? a_src[kk] : T(0);
         }
         const int kk = kc + b_k;
 #pragma unroll
         for (int e = 0; e < BPT; ++e) {
             const int c = col0 + b_c + e;
-            rb[e] = (kk < w && c < n) ? b_src[idx(kc + b_k, e, lda)] : 0.0;
+            rb[e] = (kk < w && c < n) ? b_src[idx(kc + b_k, e, lda)] : T(0);
         }
     };
     auto store_chunk = [&](int buf) {
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) schur_f64_kernel(double* __restrict__ A, 
         if (ch + 1 < nchunk) load_chunk((ch + 1) * BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            double av[TM], bv[TN];
+            T av[TM], bv[TN];
 #pragma unroll
             for (int i = 0; i < TM; ++i) av[i] = As[buf][kk][ty + 16 * i];
 #pragma unroll
@@ -104,7 +104,28 @@ int schur_f64(double* A, int lda, int m, int k, int w, int c0, int c1, cudaStrea
     dim3 grid(cdiv(N, 64), cdiv(M, 64));
     {
         ProfScope ps(LU_PROF_SCHUR, s, 2.0 * M * N * w, 8.0 * (2.0 * M * N + static_cast<double>(M + N) * w));
-        schur_f64_kernel<64, 64><<<grid, 256, 0, s>>>(A, lda, m, k, w, c0, c1);
+        schur_simt_kernel<double, 64, 64><<<grid, 256, 0, s>>>(A, lda, m, k, w, c0, c1);
+        count_launches(1);
+    }
+    LU_LAUNCHED();
+    return 0;
+}
+
+// binary32 CUDA-core variant (the all-fp32 factorization): 128 x 128 tiles,
+// 8 x 8 accumulators per thread.
+int schur_f32(float* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s) {
+    const int M = m - k - w, N = c1 - c0;
+    if (M <= 0 || N <= 0 || w <= 0) return 0;
+    const long long big = static_cast<long long>(cdiv(M, 128)) * cdiv(N, 128);
+    {
+        ProfScope ps(LU_PROF_SCHUR, s, 2.0 * M * N * w, 4.0 * (2.0 * M * N + static_cast<double>(M + N) * w));
+        if (big >= 152) {
+            dim3 grid(cdiv(N, 128), cdiv(M, 128));
+            schur_simt_kernel<float, 128, 128><<<grid, 256, 0, s>>>(A, lda, m, k, w, c0, c1);
+        } else {
+            dim3 grid(cdiv(N, 64), cdiv(M, 64));
+            schur_simt_kernel<float, 64, 64><<<grid, 256, 0, s>>>(A, lda, m, k, w, c0, c1);
+        }
         count_launches(1);
     }
     LU_LAUNCHED();

@@ -22,7 +22,7 @@ namespace cg = cooperative_groups;
 
 namespace lu {
 
-TsluShape tslu_shape(int m, int k, int w, int h, int max_cluster) {
+TsluShape tslu_shape(int m, int k, int w, int h, int max_cluster, int elem) {
     TsluShape s{};
     const int nact = m - k;
     int H = h;
@@ -34,19 +34,20 @@ TsluShape tslu_shape(int m, int k, int w, int h, int max_cluster) {
     s.nsuper = cdiv(nact, H);
     s.nr_max = (s.nsuper == 1) ? nact : (H > 2 * w ? H : 2 * w);
     int C = 1, R = s.nr_max;
-    while (C < max_cluster && static_cast<long long>(R) * (w + 1) > 4096) {
+    while (C < max_cluster && static_cast<long long>(R) * (w + 1) * elem > 32768) {
         C *= 2;
         R = cdiv(s.nr_max, C);
     }
     s.C = C;
     s.R = R;
-    s.smem = static_cast<size_t>(R) * (w + 1) * sizeof(double) + static_cast<size_t>(w) * sizeof(double) +
+    s.smem = static_cast<size_t>(R) * (w + 1) * elem + static_cast<size_t>(w) * elem +
              static_cast<size_t>(R) * 2 * sizeof(int) + static_cast<size_t>(w) * sizeof(int);
     return s;
 }
 
+template <typename T>
 struct LevelArgs {
-    const double* A;
+    const T* A;
     int lda, m, k, w, H;
     int level;          // 0: first launched level (contiguous row ranges)
     int nnode;          // nodes at this level
@@ -56,19 +57,21 @@ struct LevelArgs {
     const int* child_cnt;
     int* out_list;      // node-major, stride w
     int* out_cnt;
-    double* a00;        // root: w x w rows of the factored winners, pivot order
+    T* a00;             // root: w x w rows of the factored winners, pivot order
     int* info;          // root: first zero pivot
     int C, R;
 };
 
-__device__ __forceinline__ bool better(double v1, int p1, double v2, int p2) {
+template <typename T>
+__device__ __forceinline__ bool better(T v1, int p1, T v2, int p2) {
     return v1 > v2 || (v1 == v2 && p1 < p2);
 }
 
-__device__ __forceinline__ void warp_argmax(double& v, int& p, int& l) {
+template <typename T>
+__device__ __forceinline__ void warp_argmax(T& v, int& p, int& l) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        double ov = __shfl_down_sync(0xffffffffu, v, off);
+        T ov = __shfl_down_sync(0xffffffffu, v, off);
         int op = __shfl_down_sync(0xffffffffu, p, off);
         int ol = __shfl_down_sync(0xffffffffu, l, off);
         if (better(ov, op, v, p)) {
@@ -79,7 +82,8 @@ __device__ __forceinline__ void warp_argmax(double& v, int& p, int& l) {
     }
 }
 
-__global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs a) {
+template <typename T>
+__global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs<T> a) {
     cg::cluster_group cluster = cg::this_cluster();
     const int q = static_cast<int>(cluster.block_rank());
     const int node = blockIdx.x / a.C;
@@ -116,14 +120,14 @@ __global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs a) {
     }
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* W = reinterpret_cast<double*>(smem_raw);    // R x ws
-    double* prow = W + static_cast<size_t>(a.R) * ws;    // w
+    T* W = reinterpret_cast<T*>(smem_raw);              // R x ws
+    T* prow = W + static_cast<size_t>(a.R) * ws;         // w
     int* ids = reinterpret_cast<int*>(prow + w);          // R
     int* ord = ids + a.R;                                 // R
     int* winp = ord + a.R;                                // w
-    __shared__ double slot_v[2];
+    __shared__ T slot_v[2];
     __shared__ int slot_p[2], slot_l[2];
-    __shared__ double part_v[32];
+    __shared__ T part_v[32];
     __shared__ int part_p[32], part_l[32];
     __shared__ int s_owner, s_lr, s_pos, s_zero;
 
@@ -136,7 +140,7 @@ __global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs a) {
             ids[r] = pos;
             ord[r] = -1;
         }
-        const double* src = a.A + idx(pos, a.k, a.lda);
+        const T* src = a.A + idx(pos, a.k, a.lda);
         for (int j = lane; j < w; j += 32) W[r * ws + j] = src[j];
     }
     if (tid == 0) s_zero = -1;
@@ -145,12 +149,12 @@ __global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs a) {
     const int ns = min(nr, w);
     for (int c = 0; c < ns; ++c) {
         // 1. local argmax of |W[r][c]| over unchosen rows
-        double bv = -1.0;
+        T bv = T(-1);
         int bp = INT_MAX, bl = -1;
         for (int r = tid; r < nloc; r += blockDim.x) {
             if (ord[r] < 0) {
-                double v = fabs(W[r * ws + c]);
-                if (!(v == v)) v = INFINITY;        // a NaN row still wins: the step always has a pivot row
+                T v = abs(W[r * ws + c]);
+                if (!(v == v)) v = T(INFINITY);     // a NaN row still wins: the step always has a pivot row
                 const int p = ids[r];
                 if (better(v, p, bv, bp)) {
                     bv = v;
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs a) {
         }
         __syncthreads();
         if (warp == 0) {
-            bv = lane < nwarp ? part_v[lane] : -1.0;
+            bv = lane < nwarp ? part_v[lane] : T(-1);
             bp = lane < nwarp ? part_p[lane] : INT_MAX;
             bl = lane < nwarp ? part_l[lane] : -1;
             warp_argmax(bv, bp, bl);
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs a) {
         cluster.sync();
         // 2. cluster-wide winner, identical in every CTA
         if (warp == 0) {
-            double v = -1.0;
+            T v = T(-1);
             int p = INT_MAX, l = -1;
             if (lane < a.C) {
                 v = cluster.map_shared_rank(slot_v, lane)[c & 1];
@@ -190,7 +194,7 @@ __global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs a) {
             int o = (lane < a.C) ? lane : -1;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
-                double ov = __shfl_down_sync(0xffffffffu, v, off);
+                T ov = __shfl_down_sync(0xffffffffu, v, off);
                 int op = __shfl_down_sync(0xffffffffu, p, off);
                 int ol = __shfl_down_sync(0xffffffffu, l, off);
                 int oo = __shfl_down_sync(0xffffffffu, o, off);
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs a) {
         __syncthreads();
         const int owner = s_owner, lr = s_lr;
         // 3. pivot row from the owner's shared memory (never written again)
-        const double* rW = cluster.map_shared_rank(W, owner);
+        const T* rW = cluster.map_shared_rank(W, owner);
         for (int j = c + tid; j < w; j += blockDim.x) prow[j] = rW[lr * ws + j];
         if (tid == 0) {
             winp[c] = s_pos;
@@ -219,14 +223,14 @@ __global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs a) {
         __syncthreads();
         // 4. multipliers (one row per lane: the IEEE division is the costly
         //    binary64 operation) and rank-1 update of the unchosen local rows
-        const double pv = prow[c];
-        if (pv != 0.0) {
+        const T pv = prow[c];
+        if (pv != T(0)) {
             for (int r = tid; r < nloc; r += blockDim.x)
                 if (ord[r] < 0) W[r * ws + c] = W[r * ws + c] / pv;
             __syncthreads();
             for (int r = warp; r < nloc; r += nwarp) {
                 if (ord[r] >= 0) continue;
-                const double l = W[r * ws + c];
+                const T l = W[r * ws + c];
                 for (int j = c + 1 + lane; j < w; j += 32) W[r * ws + j] = fma(-l, prow[j], W[r * ws + j]);
             }
         } else if (tid == 0 && s_zero < 0) {
@@ -250,7 +254,8 @@ __global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs a) {
     cluster.sync();     // no CTA leaves while another may still read its shared memory
 }
 
-static int launch_level(const LevelArgs& args, int nnode, int C, size_t smem, cudaStream_t s) {
+template <typename T>
+static int launch_level(const LevelArgs<T>& args, int nnode, int C, size_t smem, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(nnode * C));
     cfg.blockDim = dim3(kTsluThreads);
@@ -264,7 +269,7 @@ static int launch_level(const LevelArgs& args, int nnode, int C, size_t smem, cu
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     ProfScope ps(LU_PROF_TSLU, s);
-    LU_TRY(cudaLaunchKernelEx(&cfg, tslu_level_kernel, args));
+    LU_TRY(cudaLaunchKernelEx(&cfg, tslu_level_kernel<T>, args));
     count_launches(1);
     return 0;
 }
@@ -275,9 +280,12 @@ int tslu_max_cluster() {
     static int cached = 0;
     if (cached) return cached;
     int best = kTsluMaxCluster;
-    if (cudaFuncSetAttribute(tslu_level_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
-        const TsluShape sh = tslu_shape(2 * kMaxPanel * 16, 0, kMaxPanel, 128, 16);
-        if (cudaFuncSetAttribute(tslu_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(tslu_level_kernel<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(tslu_level_kernel<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess) {
+        const TsluShape sh = tslu_shape(2 * kMaxPanel * 16, 0, kMaxPanel, 128, 16, sizeof(double));
+        if (cudaFuncSetAttribute(tslu_level_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(sh.smem)) == cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(16);
@@ -291,7 +299,8 @@ int tslu_max_cluster() {
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             int nclusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclusters, tslu_level_kernel, &cfg) == cudaSuccess && nclusters > 0)
+            if (cudaOccupancyMaxActiveClusters(&nclusters, tslu_level_kernel<double>, &cfg) == cudaSuccess &&
+                nclusters > 0)
                 best = 16;
         }
     }
@@ -300,14 +309,15 @@ int tslu_max_cluster() {
     return cached;
 }
 
-int tslu_select_f64(const double* A, int lda, int m, int k, int w, int h, int* lists, int* counts,
-                    size_t list_stride_nodes, double* a00, int* info, const int** root_list, cudaStream_t s) {
-    const TsluShape sh = tslu_shape(m, k, w, h, tslu_max_cluster());
-    LU_TRY(cudaFuncSetAttribute(tslu_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <typename T>
+int tslu_select(const T* A, int lda, int m, int k, int w, int h, int* lists, int* counts,
+                size_t list_stride_nodes, T* a00, int* info, const int** root_list, cudaStream_t s) {
+    const TsluShape sh = tslu_shape(m, k, w, h, tslu_max_cluster(), sizeof(T));
+    LU_TRY(cudaFuncSetAttribute(tslu_level_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(sh.smem)));
     int* list_buf[2] = {lists, lists + list_stride_nodes * w};
     int* cnt_buf[2] = {counts, counts + list_stride_nodes};
-    LevelArgs args{};
+    LevelArgs<T> args{};
     args.A = A;
     args.lda = lda;
     args.m = m;
@@ -347,6 +357,11 @@ int tslu_select_f64(const double* A, int lda, int m, int k, int w, int h, int* l
     *root_list = list_buf[cur];
     return 0;
 }
+
+template int tslu_select<double>(const double*, int, int, int, int, int, int*, int*, size_t, double*, int*,
+                                 const int**, cudaStream_t);
+template int tslu_select<float>(const float*, int, int, int, int, int, int*, int*, size_t, float*, int*, const int**,
+                                cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Pivot application.  The w winners go to rows k..k+w-1 by LAPACK-style
@@ -416,10 +431,11 @@ __global__ void pivot_moves_kernel(const int* __restrict__ win, int k, int w, in
 // One CTA per 32-column slab: read every source row segment, then write
 // every destination, then overwrite the top block's panel columns with the
 // factored A00 taken from the tournament root.
-__global__ void __launch_bounds__(256) row_move_kernel(double* __restrict__ A, int lda, int n, int k, int w,
-                                                       const int* __restrict__ mv, const double* __restrict__ a00) {
+template <typename T>
+__global__ void __launch_bounds__(256) row_move_kernel(T* __restrict__ A, int lda, int n, int k, int w,
+                                                       const int* __restrict__ mv, const T* __restrict__ a00) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* tile = reinterpret_cast<double*>(smem_raw);
+    T* tile = reinterpret_cast<T*>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int cnt = mv[0];
     const int* dst = mv + 1;
@@ -438,8 +454,9 @@ __global__ void __launch_bounds__(256) row_move_kernel(double* __restrict__ A, i
     }
 }
 
-int pivot_apply_f64(double* A, int lda, int m, int n, int k, int w, const int* root_list, const double* a00,
-                    int* piv, int* mv, cudaStream_t s) {
+template <typename T>
+int pivot_apply(T* A, int lda, int m, int n, int k, int w, const int* root_list, const T* a00, int* piv, int* mv,
+                cudaStream_t s) {
     (void)m;
     {
         ProfScope ps(LU_PROF_PIVOT, s);
@@ -447,15 +464,20 @@ int pivot_apply_f64(double* A, int lda, int m, int n, int k, int w, const int* r
         count_launches(1);
     }
     LU_LAUNCHED();
-    const size_t smem = static_cast<size_t>(2 * w) * 32 * sizeof(double);
-    LU_TRY(cudaFuncSetAttribute(row_move_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    const size_t smem = static_cast<size_t>(2 * w) * 32 * sizeof(T);
+    LU_TRY(cudaFuncSetAttribute(row_move_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(smem)));
     {
         ProfScope ps(LU_PROF_PIVOT, s);
-        row_move_kernel<<<cdiv(n, 32), 256, smem, s>>>(A, lda, n, k, w, mv, a00);
+        row_move_kernel<T><<<cdiv(n, 32), 256, smem, s>>>(A, lda, n, k, w, mv, a00);
         count_launches(1);
     }
     LU_LAUNCHED();
     return 0;
 }
+
+template int pivot_apply<double>(double*, int, int, int, int, int, const int*, const double*, int*, int*,
+                                 cudaStream_t);
+template int pivot_apply<float>(float*, int, int, int, int, int, const int*, const float*, int*, int*, cudaStream_t);
 
 }  // namespace lu
