@@ -153,6 +153,30 @@ int lu_residual(int n, int nrhs, const double *A, int lda, const double *X,
                 int ldx, const double *B, int ldb, double *R, int ldr,
                 double *eta, cudaStream_t stream);
 
+/*
+ * lu_residual_noalloc -- lu_residual for callers that must not allocate
+ * device memory while they run: a serving loop that reserves all of its
+ * memory before taking requests (so that no request can fail halfway on an
+ * out-of-memory), or a process in which another framework's caching
+ * allocator owns the GPU's memory.  The paper has no counterpart; this is a
+ * deployment variant of the residual and backward-error computation.
+ *
+ * Same arguments, results and layouts as lu_residual, with nrhs <= 64
+ * (larger nrhs returns -2 before any work).  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Its reduction scratch is one fixed
+ * array of about 160 KB per device, placed in the library and kept until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  Every call on a device uses the same
+ * array, so calls whose work overlaps on the GPU (different streams, no
+ * ordering between them) race and give wrong results; calls ordered on one
+ * stream are safe.  Nothing in the array has to start at zero: each call
+ * writes every slot it reads.
+ */
+int lu_residual_noalloc(int n, int nrhs, const double *A, int lda,
+                        const double *X, int ldx, const double *B, int ldb,
+                        double *R, int ldr, double *eta, cudaStream_t stream);
+
 /* Options and result of ir_solve.  Zero fields take defaults. */
 typedef struct {
     int precision;          /* first factorization: LU_PREC_BF16 (also when 0),

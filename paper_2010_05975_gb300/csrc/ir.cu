@@ -699,3 +699,90 @@ extern "C" int ir_solve(int n, int nrhs, const double* A, int lda, const double*
     }
     return 0;
 }
+
+// ---------------------------------------------------------------------------
+// lu_residual_noalloc: lu_residual for callers that cannot allocate device
+// memory while they run -- for example a serving loop that reserves all of
+// its memory up front so that no request can fail halfway on an allocation,
+// or a process whose GPU memory is owned by another framework's caching
+// allocator.  Its reduction scratch is a fixed array in this file instead of
+// a cudaMallocAsync buffer, which bounds nrhs.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace lu {
+
+constexpr int kNoAllocMaxRhs = 64;
+constexpr size_t kNoAllocWords =
+    static_cast<size_t>(kRedBlocks) * kNoAllocMaxRhs + 4 * static_cast<size_t>(kNoAllocMaxRhs) + kRedBlocks + 8;
+
+// Shared by every call on a device, held until the process exits (about
+// 160 KB per device that loads the library).  Every slot a call reads is
+// written earlier in the same call, so nothing has to start at zero.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocWords];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kNoAllocMaxDevices = 64;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of this device's scratch array.  In host code the array's
+// name is only a host-side stand-in, so the address comes from
+// cudaGetSymbolAddress, once per device, with that device current.
+int noalloc_scratch(double** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return LU_ELAUNCH;
+    }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return LU_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return LU_ELAUNCH;
+        }
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return 0;
+}
+}  // namespace
+}  // namespace lu
+
+extern "C" int lu_residual_noalloc(int n, int nrhs, const double* A, int lda, const double* X, int ldx,
+                                   const double* B, int ldb, double* R, int ldr, double* eta, cudaStream_t stream) {
+    using namespace lu;
+    if (n < 0) return -1;
+    if (nrhs < 0 || nrhs > kNoAllocMaxRhs) return -2;
+    if (n > 0 && (A == nullptr || lda < n)) return -3;
+    if (n > 0 && nrhs > 0 && (X == nullptr || ldx < nrhs)) return -5;
+    if (n > 0 && nrhs > 0 && (B == nullptr || ldb < nrhs)) return -7;
+    if (n > 0 && nrhs > 0 && (R == nullptr || ldr < nrhs)) return -9;
+    if (n > 0 && nrhs > 0 && eta == nullptr) return -11;
+    if (n == 0 || nrhs == 0) return 0;
+    double* ws = nullptr;
+    if (int rc = noalloc_scratch(&ws)) return rc;
+    double* part = ws;
+    double* rmax = ws + static_cast<size_t>(kRedBlocks) * kNoAllocMaxRhs;
+    double* xmax = rmax + kNoAllocMaxRhs;
+    double* bmax = xmax + kNoAllocMaxRhs;
+    double* an = bmax + kNoAllocMaxRhs;
+    residual_kernel<<<cdiv(n, kResRows), 256, 0, stream>>>(n, nrhs, A, lda, X, ldx, B, ldb, R, ldr);
+    row_abs_sum_kernel<<<kRedBlocks, 256, 0, stream>>>(n, A, lda, part);
+    max_reduce_kernel<<<1, 256, 0, stream>>>(kRedBlocks, part, an);
+    col_reduce_kernel<<<kRedBlocks, 256, 256 * sizeof(double), stream>>>(n, nrhs, R, ldr, nullptr, 0, 0, part);
+    col_fold_kernel<<<cdiv(nrhs, 64), 64, 0, stream>>>(kRedBlocks, nrhs, 0, part, rmax);
+    col_reduce_kernel<<<kRedBlocks, 256, 256 * sizeof(double), stream>>>(n, nrhs, X, ldx, nullptr, 0, 0, part);
+    col_fold_kernel<<<cdiv(nrhs, 64), 64, 0, stream>>>(kRedBlocks, nrhs, 0, part, xmax);
+    col_reduce_kernel<<<kRedBlocks, 256, 256 * sizeof(double), stream>>>(n, nrhs, B, ldb, nullptr, 0, 0, part);
+    col_fold_kernel<<<cdiv(nrhs, 64), 64, 0, stream>>>(kRedBlocks, nrhs, 0, part, bmax);
+    eta_kernel<<<cdiv(nrhs, 64), 64, 0, stream>>>(nrhs, rmax, xmax, bmax, an, eta);
+    count_launches(10);
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        cudaGetLastError();
+        return LU_ELAUNCH;
+    }
+    return 0;
+}
