@@ -59,6 +59,12 @@ def parse():
     ap.add_argument("--ref-sample-n", type=int, default=4096,
                     help="order of the matrix the CPU oracle factors in each --impl reference step")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--workload", choices=["lu64", "mixed"], default="lu64",
+                    help="lu64: the FP64 factorization (default line); mixed: only the mixed-precision "
+                         "refinement measurement")
+    ap.add_argument("--mixed-n", type=int, default=32768)
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision refinement measurement appended to the default line")
     return ap.parse_args()
 
 
@@ -172,6 +178,81 @@ def run_reference(a):
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "gpu_launches": 0}
     print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# mixed precision + binary64 refinement (A = H1 diag(s) H2, 16 right-hand sides)
+# ---------------------------------------------------------------------------
+def householder_on_device(n, kappa, seed, dev):
+    """A = H1 diag(s) H2 built on the device from the seeded reflector vectors
+    of workloads.householder_diag (input construction only, torch ops)."""
+    import torch
+    import workloads as wl
+    V1 = torch.from_numpy(wl.generators._reflectors(n, 8, seed, 1)).to(dev)
+    V2 = torch.from_numpy(wl.generators._reflectors(n, 8, seed, 2)).to(dev)
+    s = kappa ** (-torch.arange(n, dtype=torch.float64, device=dev) / max(n - 1, 1))
+    A = torch.diag(s)
+    for v in V2:
+        A.addr_(A @ v, v, alpha=-2.0)
+    for v in V1.flip(0):
+        A.addr_(v, v @ A, alpha=-2.0)
+    return A
+
+
+def run_mixed(a, dev, t_fp64_factor=None, warmup=1, steps=2, kappas=(1e2, 1e4, 1e6, 1e8)):
+    import torch
+    import paper_2010_05975_gb300 as g
+    import workloads as wl
+    n, nrhs = a.mixed_n, 16
+    out = {"n": n, "nrhs": nrhs, "tol": 1e-12, "steps": steps, "warmup": warmup, "cases": []}
+    stream = torch.cuda.current_stream(dev)
+    # plain binary64 reference form on the same GPU: lu_factor + lu_solve
+    t_solve64 = None
+    for kappa in kappas:
+        A = householder_on_device(n, kappa, int(round(np.log10(kappa))), dev)
+        Xt = torch.from_numpy(wl.matrix_normal(n, nrhs, seed=int(round(np.log10(kappa))) + 1000)).to(dev)
+        Bm = A @ Xt
+        if t_solve64 is None:
+            LU = A.clone()
+            piv, info = g.lu_factor_ex(LU, b=a.b, h=a.h)
+            Xs = Bm.clone()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.lu_solve(LU, piv, Xs)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t_solve64 = e0.elapsed_time(e1) / 1e3
+            del LU, Xs
+        for prec, pname in ((g.LU_PREC_BF16, "bf16"), (g.LU_PREC_FP8, "fp8")):
+            X = torch.empty_like(Bm)
+            for _ in range(warmup):
+                g.ir_solve(A, Bm, X=X, precision=prec)
+            times = []
+            res = None
+            for _ in range(steps):
+                torch.cuda.synchronize(dev)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, res = g.ir_solve(A, Bm, X=X, precision=prec)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                times.append(e0.elapsed_time(e1) / 1e3)
+            fwd = float(((X - Xt).abs().amax(dim=0) / Xt.abs().amax(dim=0)).max())
+            t = float(np.median(times))
+            case = {"kappa": kappa, "precision": pname, "ms": 1e3 * t, "solves_per_s": 1.0 / t,
+                    "iters": res["iters"], "gmres_iters": res["gmres_iters"], "path": res["path"],
+                    "final_precision": ["f64", "f32", "bf16", "fp8"][res["precision"]],
+                    "eta": res["eta"], "fwd_err": fwd}
+            if t_fp64_factor is not None:
+                case["speedup_vs_fp64_solve"] = (t_fp64_factor + t_solve64) / t
+            out["cases"].append(case)
+        del A, Bm, Xt
+        torch.cuda.empty_cache()
+    out["fp64_reference_s"] = None if t_fp64_factor is None else t_fp64_factor + t_solve64
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -295,6 +376,11 @@ def run_ours(a):
                 "avg_launch_ms": sch["ms"] / sch["launches"],
                 "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; the probe measured 1.19"}
     shares = {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof.items()}
+    mixed = None
+    if not a.no_mixed and world == 1:
+        del dA0, dA
+        torch.cuda.empty_cache()
+        mixed = run_mixed(a, dev, t_fp64_factor=tmax / a.steps)
 
     if rank != 0:
         if world > 1:
@@ -311,7 +397,7 @@ def run_ours(a):
            "warmup": a.warmup, "ms_per_step": 1e3 * tmax / a.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": cfg, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
-           "gpu_launches": launches, "kernel_time_ms": shares}
+           "gpu_launches": launches, "kernel_time_ms": shares, "mixed_ir": mixed}
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -321,6 +407,14 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "mixed":
+        import torch
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        torch.cuda.set_device(dev)
+        from paper_2010_05975_gb300 import build as nb
+        nb.build()
+        print(json.dumps({"metric": "IR solves/s at 1e-12 backward error", "unit": "solves/s",
+                          "mixed_ir": run_mixed(a, dev)}), flush=True)
     else:
         run_ours(a)
 
