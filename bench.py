@@ -231,6 +231,9 @@ def run_mixed(a, dev, t_fp64_factor=None, warmup=1, steps=2, kappas=(1e2, 1e4, 1
                 g.ir_solve(A, Bm, X=X, precision=prec)
             times = []
             res = None
+            g.prof_begin()
+            g.ir_solve(A, Bm, X=X, precision=prec)
+            prof = g.prof_end()
             for _ in range(steps):
                 torch.cuda.synchronize(dev)
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -245,7 +248,8 @@ def run_mixed(a, dev, t_fp64_factor=None, warmup=1, steps=2, kappas=(1e2, 1e4, 1
             case = {"kappa": kappa, "precision": pname, "ms": 1e3 * t, "solves_per_s": 1.0 / t,
                     "iters": res["iters"], "gmres_iters": res["gmres_iters"], "path": res["path"],
                     "final_precision": ["f64", "f32", "bf16", "fp8"][res["precision"]],
-                    "eta": res["eta"], "fwd_err": fwd}
+                    "eta": res["eta"], "fwd_err": fwd,
+                    "kernel_ms": {k: round(v["ms"], 2) for k, v in prof.items()}}
             if t_fp64_factor is not None:
                 case["speedup_vs_fp64_solve"] = (t_fp64_factor + t_solve64) / t
             out["cases"].append(case)

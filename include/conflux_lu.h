@@ -181,8 +181,7 @@ int lu_residual_noalloc(int n, int nrhs, const double *A, int lda,
 typedef struct {
     int precision;          /* first factorization: LU_PREC_BF16 (also when 0),
                                LU_PREC_FP8 or LU_PREC_F32                      */
-    int b, h;               /* panel width and leaf height (defaults 256/128 for
-                               n >= 4096, else 128/128)                        */
+    int b, h;               /* panel width and leaf height (defaults 128/128) */
     double tol;             /* stop when max_c eta_c <= tol (default 1e-12)    */
     int max_iter;           /* outer refinement steps (default 40)             */
     int gmres_restart;      /* FGMRES restart length (default 30, max 200)     */

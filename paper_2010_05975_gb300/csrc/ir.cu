@@ -559,7 +559,9 @@ extern "C" int ir_solve(int n, int nrhs, const double* A, int lda, const double*
         res->path = 0;
         return 0;
     }
-    int b = opt.b > 0 ? opt.b : (n >= 4096 ? 256 : 128);
+    // b = 128 for the low-precision factorizations: a binary32 tournament node
+    // (2b x b values) then fits in one CTA's shared memory.
+    int b = opt.b > 0 ? opt.b : 128;
     if (prec == LU_PREC_BF16 || prec == LU_PREC_FP8) b = (b + 127) / 128 * 128;
     if (b > 256) b = 256;
     const int h = opt.h > 0 ? opt.h : 128;

@@ -29,6 +29,7 @@ constexpr int kTcK = 256;         // padded K of every step (b <= 256)
 constexpr int kTcThreads = 192;   // 6 warps
 constexpr int kScaleTile = 256;   // operand rows/columns sharing one scale
 constexpr long long kWaitLimit = 1ll << 26;   // try_wait polls before giving up
+constexpr int kTsluReserveSMs = 16;           // SMs left to the concurrent tournament
 
 // ----------------------------------------------------------------------------
 // PTX wrappers
@@ -510,8 +511,11 @@ int schur_tc(float* C, int ldc, int M, int N, const void* Lq, const void* Uq, co
     a.status = status;
     a.vec4 = ((reinterpret_cast<uintptr_t>(C) & 15) == 0 && (ldc & 3) == 0) ? 1 : 0;
     const size_t smem = lowp_smem_bytes(fp8);
+    // The update is HBM-bound; leaving kTsluReserveSMs SMs free lets the next
+    // panel's tournament (launched concurrently by the lookahead) run beside it.
     const long long tiles = static_cast<long long>(cdiv(M, kTcBM)) * cdiv(N, kTcBN);
-    const int grid = static_cast<int>(tiles < sm_count() ? tiles : sm_count());
+    const int avail = sm_count() > 2 * kTsluReserveSMs ? sm_count() - kTsluReserveSMs : sm_count();
+    const int grid = static_cast<int>(tiles < avail ? tiles : avail);
     {
         ProfScope ps(LU_PROF_SCHUR_LP, s, 2.0 * M * N * w, 4.0 * 2.0 * M * N + (fp8 ? 1.0 : 2.0) * (M + N) * kTcK);
         if (fp8) {

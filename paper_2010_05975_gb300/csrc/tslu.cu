@@ -33,8 +33,13 @@ TsluShape tslu_shape(int m, int k, int w, int h, int max_cluster, int elem) {
     s.H = H;
     s.nsuper = cdiv(nact, H);
     s.nr_max = (s.nsuper == 1) ? nact : (H > 2 * w ? H : 2 * w);
+    // binary64: spread the node over up to max_cluster CTAs (the DFMA pipe,
+    // about 2 FMA/clk/SM, bounds each CTA's update); binary32: the fewest CTAs
+    // whose rows fit in shared memory (the cluster barrier per column is then
+    // the cost to avoid).
+    const long long budget = (elem == 8) ? 32768 : 200 * 1024;
     int C = 1, R = s.nr_max;
-    while (C < max_cluster && static_cast<long long>(R) * (w + 1) * elem > 32768) {
+    while (C < max_cluster && static_cast<long long>(R) * (w + 1) * elem > budget) {
         C *= 2;
         R = cdiv(s.nr_max, C);
     }
@@ -83,7 +88,10 @@ __device__ __forceinline__ void warp_argmax(T& v, int& p, int& l) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs<T> a) {
+constexpr int tslu_threads() { return sizeof(T) == 4 ? 512 : kTsluThreads; }
+
+template <typename T>
+__global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs<T> a) {
     cg::cluster_group cluster = cg::this_cluster();
     const int q = static_cast<int>(cluster.block_rank());
     const int node = blockIdx.x / a.C;
@@ -127,9 +135,9 @@ __global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs<T> a
     int* winp = ord + a.R;                                // w
     __shared__ T slot_v[2];
     __shared__ int slot_p[2], slot_l[2];
-    __shared__ T part_v[32];
-    __shared__ int part_p[32], part_l[32];
-    __shared__ int s_owner, s_lr, s_pos, s_zero;
+    __shared__ T part_v[2][32];
+    __shared__ int part_p[2][32], part_l[2][32];
+    __shared__ int s_owner, s_lr, s_zero;
 
     const int i0 = q * a.R;
     const int nloc = max(0, min(a.R, nr - i0));
@@ -147,97 +155,144 @@ __global__ void __launch_bounds__(kTsluThreads) tslu_level_kernel(LevelArgs<T> a
     __syncthreads();
 
     const int ns = min(nr, w);
+    // Row groups: tpr (a power of two <= 32) threads per row, all in one warp.
+    int tpr = 1;
+    while (tpr < 32 && 2 * tpr * max(nloc, 1) <= static_cast<int>(blockDim.x)) tpr *= 2;
+    const int rows_per_pass = static_cast<int>(blockDim.x) / tpr;
+    const int jj = tid % tpr;
+    const unsigned gmask = (tpr == 32) ? 0xffffffffu : (((1u << tpr) - 1u) << (lane & ~(tpr - 1)));
+    const int glead = lane & ~(tpr - 1);
+
+    // candidate of column 0 (later columns come out of the fused update)
+    T bv = T(-1);
+    int bp = INT_MAX, bl = -1;
+    if (jj == 0 && ns > 0)
+        for (int r = tid / tpr; r < nloc; r += rows_per_pass) {
+            T v = abs(W[r * ws + 0]);
+            if (!(v == v)) v = T(INFINITY);     // a NaN row still wins: the step always has a pivot row
+            if (better(v, ids[r], bv, bp)) {
+                bv = v;
+                bp = ids[r];
+                bl = r;
+            }
+        }
     for (int c = 0; c < ns; ++c) {
-        // 1. local argmax of |W[r][c]| over unchosen rows
-        T bv = T(-1);
-        int bp = INT_MAX, bl = -1;
-        for (int r = tid; r < nloc; r += blockDim.x) {
-            if (ord[r] < 0) {
-                T v = abs(W[r * ws + c]);
-                if (!(v == v)) v = T(INFINITY);     // a NaN row still wins: the step always has a pivot row
-                const int p = ids[r];
-                if (better(v, p, bv, bp)) {
+        // 1. per-warp argmax of the candidates for column c (double-buffered
+        //    partials: a warp may run one step ahead of a slow reader)
+        const int buf = c & 1;
+        warp_argmax(bv, bp, bl);
+        if (lane == 0) {
+            part_v[buf][warp] = bv;
+            part_p[buf][warp] = bp;
+            part_l[buf][warp] = bl;
+        }
+        __syncthreads();
+        int lr, owner;
+        if (a.C == 1) {
+            // one-CTA node: every thread folds the partials itself
+            T v = part_v[buf][0];
+            int p = part_p[buf][0], l = part_l[buf][0];
+            for (int i = 1; i < nwarp; ++i)
+                if (better(part_v[buf][i], part_p[buf][i], v, p)) {
+                    v = part_v[buf][i];
+                    p = part_p[buf][i];
+                    l = part_l[buf][i];
+                }
+            lr = l;
+            owner = 0;
+            if (tid == 0) winp[c] = p;
+        } else {
+            if (warp == 0) {
+                bv = lane < nwarp ? part_v[buf][lane] : T(-1);
+                bp = lane < nwarp ? part_p[buf][lane] : INT_MAX;
+                bl = lane < nwarp ? part_l[buf][lane] : -1;
+                warp_argmax(bv, bp, bl);
+                if (lane == 0) {
+                    slot_v[buf] = bv;
+                    slot_p[buf] = bp;
+                    slot_l[buf] = bl;
+                }
+            }
+            cluster.sync();
+            // 2. cluster-wide winner, identical in every CTA
+            if (warp == 0) {
+                T v = T(-1);
+                int p = INT_MAX, l = -1;
+                if (lane < a.C) {
+                    v = cluster.map_shared_rank(slot_v, lane)[buf];
+                    p = cluster.map_shared_rank(slot_p, lane)[buf];
+                    l = cluster.map_shared_rank(slot_l, lane)[buf];
+                }
+                int o = (lane < a.C) ? lane : -1;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    T ov = __shfl_down_sync(0xffffffffu, v, off);
+                    int op = __shfl_down_sync(0xffffffffu, p, off);
+                    int ol = __shfl_down_sync(0xffffffffu, l, off);
+                    int oo = __shfl_down_sync(0xffffffffu, o, off);
+                    if (better(ov, op, v, p)) {
+                        v = ov;
+                        p = op;
+                        l = ol;
+                        o = oo;
+                    }
+                }
+                if (lane == 0) {
+                    s_owner = o;
+                    s_lr = l;
+                    winp[c] = p;
+                    if (o == q) ord[l] = c;
+                }
+            }
+            __syncthreads();
+            owner = s_owner;
+            lr = s_lr;
+        }
+        // 3. the pivot row (never written again): in place for a one-CTA node,
+        //    else copied from the owner's shared memory
+        const T* pr;
+        if (a.C == 1) {
+            pr = W + lr * ws;
+        } else {
+            const T* rW = cluster.map_shared_rank(W, owner);
+            for (int j = c + tid; j < w; j += blockDim.x) prow[j] = rW[lr * ws + j];
+            __syncthreads();
+            pr = prow;
+        }
+        const T pv = pr[c];
+        if (pv == T(0) && tid == 0 && s_zero < 0) s_zero = c;
+        // 4. fused: multiplier (one division per row, shuffled to the row's
+        //    threads), rank-1 update, and the candidate for column c+1.
+        bv = T(-1);
+        bp = INT_MAX;
+        bl = -1;
+        const bool next = (c + 1 < ns);
+        for (int r = tid / tpr; r < nloc; r += rows_per_pass) {
+            if (a.C == 1 && r == lr) {                       // chosen now: mark it, leave it
+                if (jj == 0) ord[r] = c;
+                continue;
+            }
+            if (ord[r] >= 0) continue;                       // uniform over the row's threads
+            T* wr = W + r * ws;
+            if (pv != T(0)) {
+                T l = T(0);
+                if (jj == 0) l = wr[c] / pv;
+                l = __shfl_sync(gmask, l, glead);
+                if (jj == 0) wr[c] = l;
+                for (int j = c + 1 + jj; j < w; j += tpr) wr[j] = fma(-l, pr[j], wr[j]);
+            }
+            if (next && jj == 0) {
+                T v = abs(wr[c + 1]);
+                if (!(v == v)) v = T(INFINITY);
+                if (better(v, ids[r], bv, bp)) {
                     bv = v;
-                    bp = p;
+                    bp = ids[r];
                     bl = r;
                 }
             }
         }
-        warp_argmax(bv, bp, bl);
-        if (lane == 0) {
-            part_v[warp] = bv;
-            part_p[warp] = bp;
-            part_l[warp] = bl;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            bv = lane < nwarp ? part_v[lane] : T(-1);
-            bp = lane < nwarp ? part_p[lane] : INT_MAX;
-            bl = lane < nwarp ? part_l[lane] : -1;
-            warp_argmax(bv, bp, bl);
-            if (lane == 0) {
-                slot_v[c & 1] = bv;
-                slot_p[c & 1] = bp;
-                slot_l[c & 1] = bl;
-            }
-        }
-        cluster.sync();
-        // 2. cluster-wide winner, identical in every CTA
-        if (warp == 0) {
-            T v = T(-1);
-            int p = INT_MAX, l = -1;
-            if (lane < a.C) {
-                v = cluster.map_shared_rank(slot_v, lane)[c & 1];
-                p = cluster.map_shared_rank(slot_p, lane)[c & 1];
-                l = cluster.map_shared_rank(slot_l, lane)[c & 1];
-            }
-            int o = (lane < a.C) ? lane : -1;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                T ov = __shfl_down_sync(0xffffffffu, v, off);
-                int op = __shfl_down_sync(0xffffffffu, p, off);
-                int ol = __shfl_down_sync(0xffffffffu, l, off);
-                int oo = __shfl_down_sync(0xffffffffu, o, off);
-                if (better(ov, op, v, p)) {
-                    v = ov;
-                    p = op;
-                    l = ol;
-                    o = oo;
-                }
-            }
-            if (lane == 0) {
-                s_owner = o;
-                s_lr = l;
-                s_pos = p;
-            }
-        }
-        __syncthreads();
-        const int owner = s_owner, lr = s_lr;
-        // 3. pivot row from the owner's shared memory (never written again)
-        const T* rW = cluster.map_shared_rank(W, owner);
-        for (int j = c + tid; j < w; j += blockDim.x) prow[j] = rW[lr * ws + j];
-        if (tid == 0) {
-            winp[c] = s_pos;
-            if (owner == q) ord[lr] = c;
-        }
-        __syncthreads();
-        // 4. multipliers (one row per lane: the IEEE division is the costly
-        //    binary64 operation) and rank-1 update of the unchosen local rows
-        const T pv = prow[c];
-        if (pv != T(0)) {
-            for (int r = tid; r < nloc; r += blockDim.x)
-                if (ord[r] < 0) W[r * ws + c] = W[r * ws + c] / pv;
-            __syncthreads();
-            for (int r = warp; r < nloc; r += nwarp) {
-                if (ord[r] >= 0) continue;
-                const T l = W[r * ws + c];
-                for (int j = c + 1 + lane; j < w; j += 32) W[r * ws + j] = fma(-l, prow[j], W[r * ws + j]);
-            }
-        } else if (tid == 0 && s_zero < 0) {
-            s_zero = c;
-        }
-        __syncthreads();
     }
+    __syncthreads();
 
     if (q == 0) {
         for (int i = tid; i < ns; i += blockDim.x) a.out_list[static_cast<size_t>(node) * w + i] = winp[i];
@@ -258,7 +313,7 @@ template <typename T>
 static int launch_level(const LevelArgs<T>& args, int nnode, int C, size_t smem, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(nnode * C));
-    cfg.blockDim = dim3(kTsluThreads);
+    cfg.blockDim = dim3(tslu_threads<T>());
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
