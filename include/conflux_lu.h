@@ -177,6 +177,33 @@ int lu_residual_noalloc(int n, int nrhs, const double *A, int lda,
                         const double *X, int ldx, const double *B, int ldb,
                         double *R, int ldr, double *eta, cudaStream_t stream);
 
+/*
+ * lu_factor_batched -- factor `batch` independent square matrices in one
+ * persistent launch (the same tournament-pivoting LU as lu_factor, one CTA
+ * per matrix, largest matrices scheduled first).
+ *   n, lda  device int[batch]: order (0 <= n <= 1024) and leading dimension
+ *   A       device array of batch device pointers (double* or float*)
+ *   piv     device array of batch device pointers to int[n]
+ *   info    device int[batch]: as lu_factor's info, or -1 when n is out of
+ *           range, a pointer is null or lda < n (that matrix is skipped)
+ *   dtype   LU_PREC_F64 or LU_PREC_F32
+ * Panel width b = lu_batched_panel_width(n), leaf height h = 128.
+ */
+int lu_factor_batched(int batch, const int *n, void *const *A, const int *lda,
+                      int *const *piv, int *info, int dtype, cudaStream_t stream);
+
+/* Panel width the batched factorization uses for an n x n matrix. */
+int lu_batched_panel_width(int n);
+
+/*
+ * lu_solve_batched -- X = U^{-1} L^{-1} P B for each matrix of a batched
+ * factorization, one launch.  n, nrhs (1..8), lda, ldb: device int[batch];
+ * LU, piv, B: device arrays of device pointers.  B is overwritten.
+ */
+int lu_solve_batched(int batch, const int *n, const int *nrhs, void *const *LU,
+                     const int *lda, int *const *piv, void *const *B,
+                     const int *ldb, int dtype, cudaStream_t stream);
+
 /* Options and result of ir_solve.  Zero fields take defaults. */
 typedef struct {
     int precision;          /* first factorization: LU_PREC_BF16 (also when 0),

@@ -32,6 +32,9 @@ from .api import (  # noqa: F401
     lu_gemm_lowp,
     lu_residual,
     ir_solve,
+    lu_factor_batched,
+    lu_solve_batched,
+    batched_panel_width,
     prof_begin,
     prof_end,
     kernel_launch_count,

@@ -69,6 +69,10 @@ _SIGS = {
     "lu_gemm_lowp": ([I, I, I, P, I, P, I, P, I, I, P, P], I),
     "lu_residual": ([I, I, P, I, P, I, P, I, P, I, P, P], I),
     "ir_solve": ([I, I, P, I, P, I, P, I, ctypes.POINTER(ir_opts), ctypes.POINTER(ir_result), P], I),
+    "lu_factor_batched": ([I, P, P, P, P, P, I, P], I),
+    "lu_solve_batched": ([I, P, P, P, P, P, P, P, I, P], I),
+    "lu_batched_panel_width": ([I], I),
+    "lu_residual_noalloc": ([I, I, P, I, P, I, P, I, P, I, P, P], I),
     "lu_prof_begin": ([], I),
     "lu_prof_end": ([P, I, P], I),
     "lu_kernel_launch_count": ([], ctypes.c_ulonglong),

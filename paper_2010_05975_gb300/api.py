@@ -207,3 +207,62 @@ def ir_solve(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor | None = None, pr
     out = {"iters": res.iters, "gmres_iters": res.gmres_iters, "path": res.path, "info": res.info,
            "eta": res.eta, "eta0": res.eta0, "precision": res.precision, "refactors": res.refactors}
     return X, out
+
+
+def _ptr_array(tensors, device):
+    return torch.tensor([t.data_ptr() for t in tensors], dtype=torch.int64, device=device)
+
+
+def lu_factor_batched(As, stream=None):
+    """Factor a list of square CUDA matrices (all float64 or all float32,
+    n <= 1024) in one launch, in place.  Returns (pivs, info) where pivs is
+    a list of int32 CUDA tensors and info an int32 CUDA tensor (-1 marks an
+    unsupported matrix)."""
+    if not As:
+        return [], None
+    dt = As[0].dtype
+    if dt not in (torch.float64, torch.float32):
+        raise TypeError("batched matrices must be float64 or float32")
+    dev = As[0].device
+    for A in As:
+        _require(A, "A", dt, 2)
+        if A.shape[0] != A.shape[1]:
+            raise ValueError("batched matrices must be square")
+    pivs = [torch.empty(max(A.shape[0], 1), dtype=torch.int32, device=dev) for A in As]
+    n = torch.tensor([A.shape[0] for A in As], dtype=torch.int32, device=dev)
+    lda = torch.tensor([max(A.stride(0), 1) for A in As], dtype=torch.int32, device=dev)
+    pa = _ptr_array(As, dev)
+    pp = _ptr_array(pivs, dev)
+    info = torch.empty(len(As), dtype=torch.int32, device=dev)
+    prec = nat.LU_PREC_F64 if dt == torch.float64 else nat.LU_PREC_F32
+    rc = nat.library().lu_factor_batched(len(As), n.data_ptr(), pa.data_ptr(), lda.data_ptr(), pp.data_ptr(),
+                                         info.data_ptr(), prec, _stream_handle(stream))
+    nat.check("lu_factor_batched", rc)
+    # the pointer and size arrays must outlive the launch
+    lu_factor_batched._keep = (n, lda, pa, pp)
+    return [p[: A.shape[0]] for p, A in zip(pivs, As)], info
+
+
+def lu_solve_batched(LUs, pivs, Bs, stream=None):
+    """Solve each LU X = B in place (B: n x nrhs, nrhs <= 8), one launch."""
+    if not LUs:
+        return Bs
+    dev = LUs[0].device
+    dt = LUs[0].dtype
+    Bs2 = [B if B.dim() == 2 else B.view(-1, 1) for B in Bs]
+    n = torch.tensor([L.shape[0] for L in LUs], dtype=torch.int32, device=dev)
+    nr = torch.tensor([B.shape[1] for B in Bs2], dtype=torch.int32, device=dev)
+    lda = torch.tensor([max(L.stride(0), 1) for L in LUs], dtype=torch.int32, device=dev)
+    ldb = torch.tensor([max(B.stride(0), 1) for B in Bs2], dtype=torch.int32, device=dev)
+    pl, pp, pb = _ptr_array(LUs, dev), _ptr_array(pivs, dev), _ptr_array(Bs2, dev)
+    prec = nat.LU_PREC_F64 if dt == torch.float64 else nat.LU_PREC_F32
+    rc = nat.library().lu_solve_batched(len(LUs), n.data_ptr(), nr.data_ptr(), pl.data_ptr(), lda.data_ptr(),
+                                        pp.data_ptr(), pb.data_ptr(), ldb.data_ptr(), prec, _stream_handle(stream))
+    nat.check("lu_solve_batched", rc)
+    lu_solve_batched._keep = (n, nr, lda, ldb, pl, pp, pb)
+    return Bs
+
+
+def batched_panel_width(n: int) -> int:
+    """Panel width b the batched factorization uses for an n x n matrix."""
+    return int(nat.library().lu_batched_panel_width(int(n)))
