@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--ref-sample-n", type=int, default=4096,
                     help="order of the matrix the CPU oracle factors in each --impl reference step")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=["lu64", "mixed"], default="lu64",
+    ap.add_argument("--workload", choices=["lu64", "mixed", "batched"], default="lu64",
                     help="lu64: the FP64 factorization (default line); mixed: only the mixed-precision "
                          "refinement measurement")
     ap.add_argument("--mixed-n", type=int, default=32768)
@@ -260,6 +260,55 @@ def run_mixed(a, dev, t_fp64_factor=None, warmup=1, steps=2, kappas=(1e2, 1e4, 1
 
 
 # ---------------------------------------------------------------------------
+# batched: 8192 matrices, n log-uniform in [16, 1024], half with + n I
+# ---------------------------------------------------------------------------
+def run_batched(a, dev, count=8192, warmup=2, steps=3):
+    import torch
+    import paper_2010_05975_gb300 as g
+    import workloads as wl
+    sizes = wl.batch_sizes(count, 16, 1024, seed=a.seed)
+    flops = float(np.sum(2.0 * sizes.astype(np.float64) ** 3 / 3.0))
+    out = {"count": count, "sizes": "log-uniform [16, 1024]", "sum_2n3_3": flops, "steps": steps,
+           "warmup": warmup, "cases": []}
+    stream = torch.cuda.current_stream(dev)
+    gen = torch.Generator(device=dev)
+    for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        gen.manual_seed(a.seed)
+        offs = np.concatenate([[0], np.cumsum(sizes.astype(np.int64) ** 2)])
+        pristine = torch.rand(int(offs[-1]), dtype=dt, device=dev, generator=gen) * 2 - 1
+        mats0 = [pristine[offs[i]:offs[i + 1]].view(int(n), int(n)) for i, n in enumerate(sizes)]
+        for i in range(1, count, 2):
+            mats0[i].diagonal().add_(float(sizes[i]))
+        work = torch.empty_like(pristine)
+        mats = [work[offs[i]:offs[i + 1]].view(int(n), int(n)) for i, n in enumerate(sizes)]
+        rhs = [torch.ones(int(n), 1 + (i % 8), dtype=dt, device=dev) for i, n in enumerate(sizes)]
+        times, stimes = [], []
+        for it in range(warmup + steps):
+            work.copy_(pristine)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pivs, info = g.lu_factor_batched(mats)
+            e1.record(stream)
+            g.lu_solve_batched(mats, pivs, rhs)
+            e2.record(stream)
+            torch.cuda.synchronize(dev)
+            if it >= warmup:
+                times.append(e0.elapsed_time(e1) / 1e3)
+                stimes.append(e1.elapsed_time(e2) / 1e3)
+        bad = int((info != 0).sum())
+        t = float(np.median(times))
+        out["cases"].append({"dtype": name, "factor_ms": 1e3 * t, "matrices_per_s": count / t,
+                             "tflops": flops / t / 1e12, "solve_ms": 1e3 * float(np.median(stimes)),
+                             "nonzero_info": bad})
+        del pristine, work, mats0, mats, rhs
+        torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
 def traffic_per_launch(avg_flops_per_launch: float):
@@ -381,10 +430,12 @@ def run_ours(a):
                 "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; the probe measured 1.19"}
     shares = {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof.items()}
     mixed = None
+    batched = None
     if not a.no_mixed and world == 1:
         del dA0, dA
         torch.cuda.empty_cache()
         mixed = run_mixed(a, dev, t_fp64_factor=tmax / a.steps)
+        batched = run_batched(a, dev)
 
     if rank != 0:
         if world > 1:
@@ -401,7 +452,7 @@ def run_ours(a):
            "warmup": a.warmup, "ms_per_step": 1e3 * tmax / a.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": cfg, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
-           "gpu_launches": launches, "kernel_time_ms": shares, "mixed_ir": mixed}
+           "gpu_launches": launches, "kernel_time_ms": shares, "mixed_ir": mixed, "batched": batched}
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -411,14 +462,18 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    elif a.workload == "mixed":
+    elif a.workload in ("mixed", "batched"):
         import torch
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
         torch.cuda.set_device(dev)
         from paper_2010_05975_gb300 import build as nb
         nb.build()
-        print(json.dumps({"metric": "IR solves/s at 1e-12 backward error", "unit": "solves/s",
-                          "mixed_ir": run_mixed(a, dev)}), flush=True)
+        if a.workload == "mixed":
+            print(json.dumps({"metric": "IR solves/s at 1e-12 backward error", "unit": "solves/s",
+                              "mixed_ir": run_mixed(a, dev)}), flush=True)
+        else:
+            print(json.dumps({"metric": "batched LU matrices/s", "unit": "matrices/s",
+                              "batched": run_batched(a, dev)}), flush=True)
     else:
         run_ours(a)
 
