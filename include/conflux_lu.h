@@ -246,6 +246,81 @@ int ir_solve(int n, int nrhs, const double *A, int lda, const double *B,
              ir_result *res, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Serving: continuous batching of solve requests on one GPU (no counterpart
+ * in the paper; it is the request loop around the mixed-precision
+ * factorization and refinement of ir_solve).
+ * ------------------------------------------------------------------------- */
+#define SERVE_PENDING   0
+#define SERVE_RUNNING   1
+#define SERVE_DONE      2
+#define SERVE_FAILED    3
+#define SERVE_FLAG_FAIL 1       /* dry-run only: the request reports failure */
+
+typedef struct serve_t serve_t;
+
+typedef struct {
+    size_t hbm_budget_bytes;    /* device memory the server may use            */
+    int max_slots;              /* requests in flight at once (default 4)      */
+    int precision;              /* default factorization precision (BF16)      */
+    double tol;                 /* default backward-error target (1e-12)       */
+    int max_queue;              /* pending requests allowed (0: unlimited)     */
+    int dry_run;                /* 1: scheduler test mode, no device work: each
+                                   request holds its budget for a time
+                                   proportional to n^3 and computes nothing    */
+    int reserved[4];
+} serve_cfg;
+
+typedef struct {
+    int n, nrhs;                /* 1 <= nrhs <= 64                              */
+    const double *A;            /* n x n row-major, lda >= n                    */
+    int lda;
+    const double *B;            /* n x nrhs row-major, ldb >= nrhs              */
+    int ldb;
+    int device_inputs;          /* 0: A and B are host pointers; 1: device      */
+    uint64_t matrix_id;         /* nonzero: cache the factors under this id; a
+                                   later request with the same id and n must
+                                   carry the same A and reuses them            */
+    double tol;                 /* 0: the server default                        */
+    int precision;              /* 0: the server default                        */
+    int flags;                  /* SERVE_FLAG_*                                  */
+    int reserved[4];
+} serve_req;
+
+typedef struct {
+    int status;                 /* SERVE_*                                       */
+    int error;                  /* LU_E* when failed                             */
+    double eta;                 /* final backward error                          */
+    double latency_s;           /* enqueue -> done                               */
+    double queue_s;             /* enqueue -> start                              */
+    int iters, gmres_iters, path, precision;   /* as ir_result                  */
+    int cache_hit;              /* factors came from the cache                   */
+} serve_status;
+
+typedef struct {
+    size_t budget_bytes, used_bytes, peak_bytes;
+    int queued, running, peak_running;
+    long long completed, failed, cache_hits, evictions;
+    int cache_entries;
+} serve_stats;
+
+/* Create a server (its worker threads and streams) on the current device.
+ * Returns 0, -1 for a bad cfg, -2 for a null handle pointer. */
+int serve_create(const serve_cfg *cfg, serve_t **h);
+/* Copy a request and queue it.  Returns 0 with *ticket set, -2 for bad
+ * request fields, LU_EBUSY when it can never fit the budget, the queue is
+ * full or the server is stopping.  The caller may free A and B on return. */
+int serve_enqueue(serve_t *h, const serve_req *r, uint64_t *ticket);
+/* Non-blocking.  Fills st; once st->status is SERVE_DONE the solution is
+ * copied to X (host, n x nrhs row-major, may be NULL) and the ticket is
+ * retired (a later poll returns LU_ENOTFOUND); a failed request is retired
+ * the same way. */
+int serve_poll(serve_t *h, uint64_t ticket, serve_status *st, double *X);
+int serve_get_stats(serve_t *h, serve_stats *out);
+/* Stop the workers (pending requests fail, running ones finish), free the
+ * factor cache.  */
+int serve_destroy(serve_t *h);
+
+/* ---------------------------------------------------------------------------
  * Measurement hooks (no counterpart in the paper's algorithm: they time it).
  * While a session is open, every kernel launch of the library is bracketed
  * by CUDA events recorded on the launch's stream; lu_prof_end waits for

@@ -22,6 +22,7 @@ from ._native import (  # noqa: F401
     library_path,
     exported_symbols,
 )
+from .serving import Server  # noqa: F401
 from .api import (  # noqa: F401
     lu_factor,
     lu_factor_ex,

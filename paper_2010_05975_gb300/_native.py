@@ -46,6 +46,37 @@ class ir_result(ctypes.Structure):
                 ("precision", ctypes.c_int), ("refactors", ctypes.c_int)]
 
 
+class serve_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("precision", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_queue", ctypes.c_int), ("dry_run", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
+
+
+class serve_req(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("nrhs", ctypes.c_int), ("A", ctypes.c_void_p), ("lda", ctypes.c_int),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int), ("device_inputs", ctypes.c_int),
+                ("matrix_id", ctypes.c_uint64), ("tol", ctypes.c_double), ("precision", ctypes.c_int),
+                ("flags", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+class serve_status(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("error", ctypes.c_int), ("eta", ctypes.c_double),
+                ("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double), ("iters", ctypes.c_int),
+                ("gmres_iters", ctypes.c_int), ("path", ctypes.c_int), ("precision", ctypes.c_int),
+                ("cache_hit", ctypes.c_int)]
+
+
+class serve_stats(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
+                ("queued", ctypes.c_int), ("running", ctypes.c_int), ("peak_running", ctypes.c_int),
+                ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong), ("cache_hits", ctypes.c_longlong),
+                ("evictions", ctypes.c_longlong), ("cache_entries", ctypes.c_int)]
+
+
+SERVE_PENDING, SERVE_RUNNING, SERVE_DONE, SERVE_FAILED = 0, 1, 2, 3
+SERVE_FLAG_FAIL = 1
+
+
 class lu_prof_entry(ctypes.Structure):
     _fields_ = [("kernel_class", ctypes.c_int), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double),
                 ("total_flops", ctypes.c_double), ("total_bytes", ctypes.c_double)]
@@ -73,6 +104,11 @@ _SIGS = {
     "lu_solve_batched": ([I, P, P, P, P, P, P, P, I, P], I),
     "lu_batched_panel_width": ([I], I),
     "lu_residual_noalloc": ([I, I, P, I, P, I, P, I, P, I, P, P], I),
+    "serve_create": ([ctypes.POINTER(serve_cfg), ctypes.POINTER(P)], I),
+    "serve_enqueue": ([P, ctypes.POINTER(serve_req), ctypes.POINTER(ctypes.c_uint64)], I),
+    "serve_poll": ([P, ctypes.c_uint64, ctypes.POINTER(serve_status), P], I),
+    "serve_get_stats": ([P, ctypes.POINTER(serve_stats)], I),
+    "serve_destroy": ([P], I),
     "lu_prof_begin": ([], I),
     "lu_prof_end": ([P, I, P], I),
     "lu_kernel_launch_count": ([], ctypes.c_ulonglong),

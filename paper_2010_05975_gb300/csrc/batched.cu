@@ -526,9 +526,7 @@ static int factor_batched(int batch, const int* n, T* const* A, const int* lda, 
     }
     if (!rc) {
         const size_t smem = sizeof(bat::Smem<T>);
-        if (cudaFuncSetAttribute(bat::batched_lu_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem)) != cudaSuccess)
-            rc = LU_ELAUNCH;
+        rc = smem_attr(bat::batched_lu_kernel<T>, smem);
         int per_sm = 0;
         if (!rc && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bat::batched_lu_kernel<T>, bat::kThreads,
                                                                  smem) != cudaSuccess)
@@ -578,14 +576,12 @@ extern "C" int lu_solve_batched(int batch, const int* n, const int* nrhs, void* 
     ProfScope ps(LU_PROF_SOLVE, stream);
     if (dtype == LU_PREC_F64) {
         const size_t smem = 8 * static_cast<size_t>(bat::kMaxN) * sizeof(double);
-        LU_TRY(cudaFuncSetAttribute(bat::batched_solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(smem)));
+        if (int rc_ = smem_attr(bat::batched_solve_kernel<double>, smem)) return rc_;
         bat::batched_solve_kernel<double><<<grid, bat::kThreads, smem, stream>>>(
             batch, n, nrhs, reinterpret_cast<double* const*>(LU), lda, piv, reinterpret_cast<double* const*>(B), ldb);
     } else if (dtype == LU_PREC_F32) {
         const size_t smem = 8 * static_cast<size_t>(bat::kMaxN) * sizeof(float);
-        LU_TRY(cudaFuncSetAttribute(bat::batched_solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(smem)));
+        if (int rc_ = smem_attr(bat::batched_solve_kernel<float>, smem)) return rc_;
         bat::batched_solve_kernel<float><<<grid, bat::kThreads, smem, stream>>>(
             batch, n, nrhs, reinterpret_cast<float* const*>(LU), lda, piv, reinterpret_cast<float* const*>(B), ldb);
     } else {

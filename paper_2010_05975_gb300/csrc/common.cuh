@@ -4,6 +4,9 @@
 #include <cstdint>
 #include <cstddef>
 #include "../../include/conflux_lu.h"
+#include <map>
+#include <mutex>
+#include <utility>
 
 #define LU_TRY(expr)                                                  \
     do {                                                              \
@@ -20,6 +23,30 @@
     } while (0)
 
 namespace lu {
+
+// Raise a kernel's dynamic shared-memory cap to at least `bytes` (per kernel
+// and device; never lowered, so concurrent callers with different sizes on
+// other host threads cannot shrink it under each other).
+template <typename K>
+inline int smem_attr(K* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return LU_ELAUNCH;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = done[std::make_pair(reinterpret_cast<const void*>(kernel), dev)];
+    if (cur >= bytes) return 0;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return LU_ELAUNCH;
+    }
+    cur = bytes;
+    return 0;
+}
 
 constexpr int kMaxPanel = 256;          // largest supported panel width b
 constexpr int kTsluThreads = 256;       // threads per tournament CTA
@@ -63,6 +90,21 @@ int schur_f64(double* A, int lda, int m, int k, int w, int c0, int c1, cudaStrea
 int schur_f32(float* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s);
 int getrs_f64(int n, int nrhs, const double* LU, int lda, const int* piv, double* B, int ldb, cudaStream_t s);
 int getrs_f32(int n, int nrhs, const float* LU, int lda, const int* piv, float* B, int ldb, cudaStream_t s);
+
+// Factorization + refinement pieces of the solver (csrc/ir.cu), shared with
+// the serving runtime.
+struct IrFactors {
+    int n = 0;
+    float* A32 = nullptr;      // binary32 factors
+    int* piv = nullptr;
+    int* info = nullptr;
+    int precision = 0;         // LU_PREC_* of the factors
+};
+int ir_factor(int n, const double* A, int lda, int prec, int b, int h, IrFactors* f, cudaStream_t s);
+int ir_refine(IrFactors* f, const double* A, int lda, int nrhs, const double* B, int ldb, double* X, int ldx,
+              const ir_opts* o, ir_result* res, cudaStream_t s);
+void ir_release(IrFactors* f, cudaStream_t s);
+size_t ir_workspace_bytes(int n, int nrhs, int restart);
 
 // Low-precision tensor-core Schur update (csrc/schur_lowp.cu).
 constexpr int kLowpK = 256;     // operand K is padded to this

@@ -184,8 +184,7 @@ int getrs_impl(int n, int nrhs, const T* LU, int lda, const int* piv, T* B, int 
     constexpr int NB = SolveNB<T>::value;
     if (n <= kPermSmemMax) {
         const size_t smem = static_cast<size_t>(n) * sizeof(int);
-        LU_TRY(cudaFuncSetAttribute(perm_from_piv_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(smem)));
+        if (int rc_ = smem_attr(perm_from_piv_smem, smem)) return rc_;
         ProfScope ps(LU_PROF_SOLVE, s);
         perm_from_piv_smem<<<1, 256, smem, s>>>(n, piv, perm);
         count_launches(1);
@@ -206,15 +205,14 @@ int getrs_impl(int n, int nrhs, const T* LU, int lda, const int* piv, T* B, int 
     LU_LAUNCHED();
     {
         const size_t ismem = 2 * static_cast<size_t>(NB) * (NB + 1) * sizeof(T);
-        LU_TRY(cudaFuncSetAttribute(invert_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(ismem)));
+        if (int rc_ = smem_attr(invert_diag_kernel<T>, ismem)) return rc_;
         ProfScope ps(LU_PROF_SOLVE, s);
         invert_diag_kernel<T><<<dim3(nblk, 2), 128, ismem, s>>>(n, LU, lda, Dinv);
         count_launches(1);
     }
     LU_LAUNCHED();
     const size_t usmem = static_cast<size_t>(NB) * nrhs * sizeof(T);
-    LU_TRY(cudaFuncSetAttribute(block_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(usmem)));
+    if (int rc_ = smem_attr(block_update<T>, usmem)) return rc_;
     auto update_grid = [&](int rows) {
         const long long work = (nrhs >= 8) ? static_cast<long long>(rows) * nrhs : static_cast<long long>(rows) * 32;
         const long long g = (work + 255) / 256;

@@ -537,35 +537,64 @@ int fgmres_cycle(IrCtx& c, int m, double gtol, double* V, double* Z, double* W, 
 }  // namespace
 }  // namespace lu
 
-extern "C" int ir_solve(int n, int nrhs, const double* A, int lda, const double* B, int ldb, double* X, int ldx,
-                        const ir_opts* o, ir_result* res, cudaStream_t stream) {
-    using namespace lu;
-    if (n < 0) return -1;
-    if (nrhs < 0 || nrhs > 384) return -2;
-    if (n > 0 && (A == nullptr || lda < n)) return -3;
-    if (n > 0 && nrhs > 0 && (B == nullptr || ldb < nrhs)) return -5;
-    if (n > 0 && nrhs > 0 && (X == nullptr || ldx < nrhs)) return -7;
-    if (res == nullptr) return -10;
+namespace lu {
+
+// Factor a binary32 copy of A at `prec` (LU_PREC_FP8 / BF16 / F32).
+int ir_factor(int n, const double* A, int lda, int prec, int b, int h, IrFactors* f, cudaStream_t s) {
+    if (f->A32 == nullptr) {
+        if (cudaMallocAsync(reinterpret_cast<void**>(&f->A32), static_cast<size_t>(n) * n * sizeof(float) + 16, s) !=
+                cudaSuccess ||
+            cudaMallocAsync(reinterpret_cast<void**>(&f->piv), static_cast<size_t>(n) * sizeof(int) + 16, s) !=
+                cudaSuccess ||
+            cudaMallocAsync(reinterpret_cast<void**>(&f->info), 2 * sizeof(int), s) != cudaSuccess) {
+            cudaGetLastError();
+            return LU_ENOMEM;
+        }
+    }
+    f->n = n;
+    {
+        ProfScope ps(LU_PROF_OTHER, s);
+        convert_matrix_f32<<<grid_for(static_cast<long long>(n) * n), 256, 0, s>>>(n, A, lda, f->A32);
+        count_launches(1);
+    }
+    LU_LAUNCHED();
+    lu_opts fo{};
+    fo.b = (prec == LU_PREC_BF16 || prec == LU_PREC_FP8) ? (b + 127) / 128 * 128 : b;
+    if (fo.b > 256) fo.b = 256;
+    fo.h = h;
+    fo.precision = prec;
+    f->precision = prec;
+    return lu_factor_f32(n, n, f->A32, n, f->piv, f->info, &fo, s);
+}
+
+void ir_release(IrFactors* f, cudaStream_t s) {
+    if (f->A32) cudaFreeAsync(f->A32, s);
+    if (f->piv) cudaFreeAsync(f->piv, s);
+    if (f->info) cudaFreeAsync(f->info, s);
+    f->A32 = nullptr;
+    f->piv = nullptr;
+    f->info = nullptr;
+}
+
+// Refinement with existing factors (which the ladder may replace by a
+// higher-precision factorization).  x0 = M^{-1} B unless keep_x.
+int ir_refine(IrFactors* fac, const double* A, int lda, int nrhs, const double* B, int ldb, double* X, int ldx,
+              const ir_opts* o, ir_result* res, cudaStream_t stream) {
+    const int n = fac->n;
     ir_opts opt{};
     if (o) opt = *o;
-    int prec = opt.precision ? opt.precision : LU_PREC_BF16;
-    if (prec < LU_PREC_F64 || prec > LU_PREC_FP8) return -9;
     const double tol = opt.tol > 0.0 ? opt.tol : 1e-12;
     const int max_iter = opt.max_iter > 0 ? opt.max_iter : 40;
     const int restart = opt.gmres_restart > 0 ? (opt.gmres_restart < 200 ? opt.gmres_restart : 200) : 30;
+    const int b = opt.b > 0 ? opt.b : 128;
+    const int h = opt.h > 0 ? opt.h : 128;
     *res = ir_result{};
     res->path = -1;
+    res->precision = fac->precision;
     if (n == 0 || nrhs == 0) {
         res->path = 0;
         return 0;
     }
-    // b = 128 for the low-precision factorizations: a binary32 tournament node
-    // (2b x b values) then fits in one CTA's shared memory.
-    int b = opt.b > 0 ? opt.b : 128;
-    if (prec == LU_PREC_BF16 || prec == LU_PREC_FP8) b = (b + 127) / 128 * 128;
-    if (b > 256) b = 256;
-    const int h = opt.h > 0 ? opt.h : 128;
-
     Dev dev;
     dev.s = stream;
     IrCtx c{};
@@ -578,10 +607,9 @@ extern "C" int ir_solve(int n, int nrhs, const double* A, int lda, const double*
     c.X = X;
     c.ldx = ldx;
     c.s = stream;
+    c.A32 = fac->A32;
+    c.piv = fac->piv;
     const size_t vs = static_cast<size_t>(n) * nrhs;
-    c.A32 = dev.alloc<float>(static_cast<size_t>(n) * n);
-    c.piv = dev.alloc<int>(n);
-    int* info = dev.alloc<int>(1);
     c.R = dev.alloc<double>(vs);
     c.r32 = dev.alloc<float>(vs);
     const size_t part_words = static_cast<size_t>(kRedBlocks) * nrhs * 4 + static_cast<size_t>(restart + 2) * 16 * nrhs;
@@ -590,74 +618,49 @@ extern "C" int ir_solve(int n, int nrhs, const double* A, int lda, const double*
     c.an = dev.alloc<double>(1);
     double* bmax = dev.alloc<double>(nrhs);
     if (!dev.ok) return LU_ENOMEM;
-
-    const size_t words_v = vs;
-    (void)words_v;
     double* V = nullptr;
     double* Z = nullptr;
     double* W = nullptr;
     double* H = nullptr;
     if (int rc = matrix_inf_norm(n, A, lda, c.part, c.an, stream)) return rc;
     if (int rc = col_reduce(n, nrhs, B, ldb, nullptr, 0, 0, c.part, bmax, stream)) return rc;
+    LU_TRY(cudaMemcpyAsync(&res->info, fac->info, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    // x0 = M^{-1} b
+    {
+        ProfScope ps(LU_PROF_OTHER, stream);
+        to_f32_scaled<<<grid_for(static_cast<long long>(vs)), 256, 0, stream>>>(n, nrhs, B, ldb, bmax, c.r32);
+        count_launches(1);
+    }
+    LU_LAUNCHED();
+    if (int rc = getrs_f32(n, nrhs, c.A32, n, c.piv, c.r32, nrhs, stream)) return rc;
+    {
+        ProfScope ps(LU_PROF_OTHER, stream);
+        from_f32_scaled<<<grid_for(static_cast<long long>(vs)), 256, 0, stream>>>(n, nrhs, c.r32, bmax, X, ldx, 0);
+        count_launches(1);
+    }
+    LU_LAUNCHED();
+    LU_TRY(cudaStreamSynchronize(stream));
+    if (res->info < 0) return LU_ETIMEOUT;
 
-    // Precision ladder: the requested factorization first; when its
-    // refinement stalls, refactor one step up (fp8 -> bf16 -> fp32) and keep
-    // refining the current X.
-    int ladder[3], nlad = 0;
-    if (prec == LU_PREC_FP8) ladder[nlad++] = LU_PREC_FP8;
-    if (prec == LU_PREC_FP8 || prec == LU_PREC_BF16) ladder[nlad++] = LU_PREC_BF16;
-    ladder[nlad++] = LU_PREC_F32;
+    // Precision ladder: the current factorization first; when its refinement
+    // stalls, refactor one step up (fp8 -> bf16 -> fp32) and keep refining
+    // the current X.
     std::vector<double> eta(nrhs);
     int total_it = 0;
-    for (int lvl = 0; lvl < nlad; ++lvl) {
-        const bool last = (lvl == nlad - 1);
-        // 1. factor a binary32 copy
-        {
-            ProfScope ps(LU_PROF_OTHER, stream);
-            convert_matrix_f32<<<grid_for(static_cast<long long>(n) * n), 256, 0, stream>>>(n, A, lda, c.A32);
-            count_launches(1);
-        }
-        LU_LAUNCHED();
-        lu_opts fo{};
-        fo.b = (ladder[lvl] == LU_PREC_F32) ? (opt.b > 0 ? opt.b : b) : b;
-        fo.h = h;
-        fo.precision = ladder[lvl];
-        if (int rc = lu_factor_f32(n, n, c.A32, n, c.piv, info, &fo, stream)) return rc;
-        LU_TRY(cudaMemcpyAsync(&res->info, info, sizeof(int), cudaMemcpyDeviceToHost, stream));
-        res->precision = ladder[lvl];
-        res->refactors = lvl;
-        if (lvl == 0) {
-            // 2. the first solve x0 = M^{-1} b
-            {
-                ProfScope ps(LU_PROF_OTHER, stream);
-                to_f32_scaled<<<grid_for(static_cast<long long>(vs)), 256, 0, stream>>>(n, nrhs, B, ldb, bmax,
-                                                                                        c.r32);
-                count_launches(1);
-            }
-            LU_LAUNCHED();
-            if (int rc = getrs_f32(n, nrhs, c.A32, n, c.piv, c.r32, nrhs, stream)) return rc;
-            {
-                ProfScope ps(LU_PROF_OTHER, stream);
-                from_f32_scaled<<<grid_for(static_cast<long long>(vs)), 256, 0, stream>>>(n, nrhs, c.r32, bmax, X,
-                                                                                          ldx, 0);
-                count_launches(1);
-            }
-            LU_LAUNCHED();
-        }
-        LU_TRY(cudaStreamSynchronize(stream));
-        if (res->info < 0) return LU_ETIMEOUT;
-
-        // 3. refinement at this level
+    for (;;) {
+        const bool last = (fac->precision == LU_PREC_F32);
         double prev = 0.0;
         bool krylov = false;
         int cycles = 0;
+        bool escalate = false;
         for (;;) {
             if (int rc = backward_error(c, eta.data(), bmax)) return rc;
             double em = 0.0;
             for (double e : eta) em = e > em ? e : em;
-            if (total_it == 0 && lvl == 0) res->eta0 = em;
+            if (total_it == 0 && res->refactors == 0) res->eta0 = em;
             res->eta = em;
             res->iters = total_it;
+            res->precision = fac->precision;
             if (em <= tol) {
                 res->path = krylov ? 1 : 0;
                 return 0;
@@ -665,14 +668,16 @@ extern "C" int ir_solve(int n, int nrhs, const double* A, int lda, const double*
             if (total_it >= max_iter) return 0;
             // stall tests: a Krylov cycle that gains less than 10x, or two
             // cycles without reaching tol, move up the ladder
-            if (krylov && !last && (cycles >= 2 || em > 0.1 * prev)) break;
+            if (krylov && !last && (cycles >= 2 || em > 0.1 * prev)) {
+                escalate = true;
+                break;
+            }
             // classical refinement while it contracts by at least 4x per step
             if (!krylov && prev > 0.0 && em > 0.25 * prev) krylov = true;
             prev = em;
             ++total_it;
             if (!krylov) {
                 if (int rc = precond_apply(c, c.R, c.R, c.vec)) return rc;
-                // X += d  (d now in R)
                 double* one = c.vec + 5 * nrhs;
                 std::vector<double> ones(nrhs, 1.0);
                 LU_TRY(cudaMemcpyAsync(one, ones.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, stream));
@@ -698,8 +703,52 @@ extern "C" int ir_solve(int n, int nrhs, const double* A, int lda, const double*
                 ++cycles;
             }
         }
+        if (!escalate) return 0;
+        const int up = (fac->precision == LU_PREC_FP8) ? LU_PREC_BF16 : LU_PREC_F32;
+        if (int rc = ir_factor(n, A, lda, up, b, h, fac, stream)) return rc;
+        res->refactors += 1;
+        LU_TRY(cudaMemcpyAsync(&res->info, fac->info, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        LU_TRY(cudaStreamSynchronize(stream));
+        if (res->info < 0) return LU_ETIMEOUT;
     }
-    return 0;
+}
+
+size_t ir_workspace_bytes(int n, int nrhs, int restart) {
+    const size_t vs = static_cast<size_t>(n) * nrhs;
+    if (restart <= 0) restart = 30;
+    return vs * (8 + 4 + 8 * (2 * static_cast<size_t>(restart) + 2)) +
+           (static_cast<size_t>(kRedBlocks) * nrhs * 4 + static_cast<size_t>(restart + 2) * 16 * nrhs + 16 * nrhs) * 8 +
+           4096;
+}
+
+}  // namespace lu
+
+extern "C" int ir_solve(int n, int nrhs, const double* A, int lda, const double* B, int ldb, double* X, int ldx,
+                        const ir_opts* o, ir_result* res, cudaStream_t stream) {
+    using namespace lu;
+    if (n < 0) return -1;
+    if (nrhs < 0 || nrhs > 384) return -2;
+    if (n > 0 && (A == nullptr || lda < n)) return -3;
+    if (n > 0 && nrhs > 0 && (B == nullptr || ldb < nrhs)) return -5;
+    if (n > 0 && nrhs > 0 && (X == nullptr || ldx < nrhs)) return -7;
+    if (res == nullptr) return -10;
+    ir_opts opt{};
+    if (o) opt = *o;
+    const int prec = opt.precision ? opt.precision : LU_PREC_BF16;
+    if (prec < LU_PREC_F64 || prec > LU_PREC_FP8) return -9;
+    *res = ir_result{};
+    res->path = -1;
+    if (n == 0 || nrhs == 0) {
+        res->path = 0;
+        return 0;
+    }
+    IrFactors fac{};
+    const int b = opt.b > 0 ? opt.b : 128;
+    const int h = opt.h > 0 ? opt.h : 128;
+    int rc = ir_factor(n, A, lda, prec == LU_PREC_F64 ? LU_PREC_F32 : prec, b, h, &fac, stream);
+    if (!rc) rc = ir_refine(&fac, A, lda, nrhs, B, ldb, X, ldx, &opt, res, stream);
+    ir_release(&fac, stream);
+    return rc;
 }
 
 // ---------------------------------------------------------------------------

@@ -519,12 +519,10 @@ int schur_tc(float* C, int ldc, int M, int N, const void* Lq, const void* Uq, co
     {
         ProfScope ps(LU_PROF_SCHUR_LP, s, 2.0 * M * N * w, 4.0 * 2.0 * M * N + (fp8 ? 1.0 : 2.0) * (M + N) * kTcK);
         if (fp8) {
-            LU_TRY(cudaFuncSetAttribute(schur_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        static_cast<int>(smem)));
+            if (int rc_ = smem_attr(schur_tc_kernel<true>, smem)) return rc_;
             schur_tc_kernel<true><<<grid, kTcThreads, smem, s>>>(tmL, tmU, a);
         } else {
-            LU_TRY(cudaFuncSetAttribute(schur_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        static_cast<int>(smem)));
+            if (int rc_ = smem_attr(schur_tc_kernel<false>, smem)) return rc_;
             schur_tc_kernel<false><<<grid, kTcThreads, smem, s>>>(tmL, tmU, a);
         }
         count_launches(1);

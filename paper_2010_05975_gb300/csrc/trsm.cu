@@ -71,7 +71,7 @@ int trsm_l21(E* A, int lda, int m, int k, int w, cudaStream_t s) {
     const int rows = m - k - w;
     if (rows <= 0) return 0;
     const size_t smem = static_cast<size_t>(w) * kL21Stride * sizeof(E);
-    LU_TRY(cudaFuncSetAttribute(trsm_l21_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    if (int rc_ = smem_attr(trsm_l21_kernel<E>, smem)) return rc_;
     {
         ProfScope ps(LU_PROF_TRSM_L21, s, static_cast<double>(rows) * w * w);
         trsm_l21_kernel<E><<<cdiv(rows, kL21Rows), 256, smem, s>>>(A, lda, m, k, w);
@@ -86,7 +86,7 @@ int trsm_u12(E* A, int lda, int n, int k, int w, cudaStream_t s) {
     const int cols = n - k - w;
     if (cols <= 0 || w <= 1) return 0;
     const size_t smem = static_cast<size_t>(w) * kU12Cols * sizeof(E);
-    LU_TRY(cudaFuncSetAttribute(trsm_u12_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    if (int rc_ = smem_attr(trsm_u12_kernel<E>, smem)) return rc_;
     {
         ProfScope ps(LU_PROF_TRSM_U12, s, static_cast<double>(cols) * w * (w - 1));
         trsm_u12_kernel<E><<<cdiv(cols, kU12Cols), 256, smem, s>>>(A, lda, n, k, w);

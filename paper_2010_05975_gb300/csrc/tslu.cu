@@ -332,35 +332,36 @@ static int launch_level(const LevelArgs<T>& args, int nnode, int C, size_t smem,
 // Largest cluster the device runs for the tournament kernel: 16 where the
 // non-portable size is available, else the portable 8.
 int tslu_max_cluster() {
-    static int cached = 0;
-    if (cached) return cached;
-    int best = kTsluMaxCluster;
-    if (cudaFuncSetAttribute(tslu_level_kernel<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-            cudaSuccess &&
-        cudaFuncSetAttribute(tslu_level_kernel<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-            cudaSuccess) {
-        const TsluShape sh = tslu_shape(2 * kMaxPanel * 16, 0, kMaxPanel, 128, 16, sizeof(double));
-        if (cudaFuncSetAttribute(tslu_level_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(sh.smem)) == cudaSuccess) {
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(16);
-            cfg.blockDim = dim3(kTsluThreads);
-            cfg.dynamicSmemBytes = sh.smem;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = 16;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            int nclusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclusters, tslu_level_kernel<double>, &cfg) == cudaSuccess &&
-                nclusters > 0)
-                best = 16;
+    static std::once_flag once;
+    static int cached = kTsluMaxCluster;
+    std::call_once(once, [] {
+        int best = kTsluMaxCluster;
+        if (cudaFuncSetAttribute(tslu_level_kernel<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(tslu_level_kernel<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess) {
+            const TsluShape sh = tslu_shape(2 * kMaxPanel * 16, 0, kMaxPanel, 128, 16, sizeof(double));
+            if (smem_attr(tslu_level_kernel<double>, sh.smem) == 0) {
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(16);
+                cfg.blockDim = dim3(kTsluThreads);
+                cfg.dynamicSmemBytes = sh.smem;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = 16;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                int nclusters = 0;
+                if (cudaOccupancyMaxActiveClusters(&nclusters, tslu_level_kernel<double>, &cfg) == cudaSuccess &&
+                    nclusters > 0)
+                    best = 16;
+            }
         }
-    }
-    cudaGetLastError();
-    cached = best;
+        cudaGetLastError();
+        cached = best;
+    });
     return cached;
 }
 
@@ -368,8 +369,7 @@ template <typename T>
 int tslu_select(const T* A, int lda, int m, int k, int w, int h, int* lists, int* counts,
                 size_t list_stride_nodes, T* a00, int* info, const int** root_list, cudaStream_t s) {
     const TsluShape sh = tslu_shape(m, k, w, h, tslu_max_cluster(), sizeof(T));
-    LU_TRY(cudaFuncSetAttribute(tslu_level_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(sh.smem)));
+    if (int rc_ = smem_attr(tslu_level_kernel<T>, sh.smem)) return rc_;
     int* list_buf[2] = {lists, lists + list_stride_nodes * w};
     int* cnt_buf[2] = {counts, counts + list_stride_nodes};
     LevelArgs<T> args{};
@@ -520,8 +520,7 @@ int pivot_apply(T* A, int lda, int m, int n, int k, int w, const int* root_list,
     }
     LU_LAUNCHED();
     const size_t smem = static_cast<size_t>(2 * w) * 32 * sizeof(T);
-    LU_TRY(cudaFuncSetAttribute(row_move_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(smem)));
+    if (int rc_ = smem_attr(row_move_kernel<T>, smem)) return rc_;
     {
         ProfScope ps(LU_PROF_PIVOT, s);
         row_move_kernel<T><<<cdiv(n, 32), 256, smem, s>>>(A, lda, n, k, w, mv, a00);

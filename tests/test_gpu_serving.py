@@ -1,0 +1,87 @@
+"""Serving on the GPU: every request reaches 1e-12 backward error, its result
+is the same alone and in the mix (bit for bit: each request runs the same
+deterministic kernels on its own stream), the factor cache is reused, a
+failing request does not disturb the others, and the budget holds."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from tests.gpu_util import cuda_or_fail, lib
+
+pytestmark = pytest.mark.gpu
+
+
+def problems():
+    rng_sizes = [32, 100, 257, 512, 1000, 64, 2048, 300, 777, 128]
+    out = []
+    for i, n in enumerate(rng_sizes):
+        kappa = 10.0 ** (1 + (i % 6))
+        A, V1, V2, s = wl.householder_diag(n, kappa, seed=100 + i)
+        nrhs = [1, 64, 7, 16, 3, 33, 16, 1, 8, 64][i]
+        Xt = wl.matrix_normal(n, nrhs, seed=200 + i)
+        out.append((A, A @ Xt, Xt, kappa))
+    return out
+
+
+def test_mix_equals_alone_and_reaches_tolerance(oracle_mod):
+    cuda_or_fail()
+    g = lib()
+    probs = problems()
+    budget = 24 << 30
+    with g.Server(budget, max_slots=4) as srv:
+        tickets = [srv.enqueue(A, B) for A, B, _, _ in probs]
+        mixed = srv.wait(tickets)
+        st = srv.stats()
+    assert st["peak_bytes"] <= budget and st["peak_running"] > 1
+    alone = []
+    with g.Server(budget, max_slots=1) as srv:
+        for A, B, _, _ in probs:
+            t = srv.enqueue(A, B)
+            alone.append(srv.wait([t])[t])
+    for (A, B, Xt, kappa), t, ra in zip(probs, tickets, alone):
+        rm = mixed[t]
+        assert rm["status"] == "done" and ra["status"] == "done", (rm, ra)
+        assert oracle_mod.backward_error(A, B, rm["X"]).max() <= 1e-12
+        np.testing.assert_array_equal(rm["X"], ra["X"])
+        fwd = np.abs(rm["X"] - Xt).max() / np.abs(Xt).max()
+        assert fwd <= 10 * kappa * 1e-12
+
+
+def test_factor_cache_reuse(oracle_mod):
+    cuda_or_fail()
+    g = lib()
+    A, V1, V2, s = wl.householder_diag(700, 1e3, seed=5)
+    B1 = wl.matrix_normal(700, 4, seed=6)
+    B2 = wl.matrix_normal(700, 4, seed=7)
+    with g.Server(8 << 30, max_slots=2) as srv:
+        t1 = srv.enqueue(A, B1, matrix_id=42)
+        r1 = srv.wait([t1])[t1]
+        t2 = srv.enqueue(A, B2, matrix_id=42)
+        r2 = srv.wait([t2])[t2]
+    assert r1["cache_hit"] == 0 and r2["cache_hit"] == 1
+    assert oracle_mod.backward_error(A, B2, r2["X"]).max() <= 1e-12
+
+
+def test_singular_request_fails_alone():
+    cuda_or_fail()
+    g = lib()
+    n = 300
+    bad = np.zeros((n, n))
+    good = [wl.householder_diag(n, 1e2, seed=i)[0] for i in range(3)]
+    with g.Server(8 << 30, max_slots=2) as srv:
+        tb = srv.enqueue(bad, np.ones((n, 1)))
+        tg = [srv.enqueue(A, np.ones((n, 2))) for A in good]
+        res = srv.wait([tb] + tg)
+    assert res[tb]["status"] == "failed"
+    assert all(res[t]["status"] == "done" and res[t]["eta"] <= 1e-12 for t in tg)
+
+
+def test_device_inputs():
+    torch = cuda_or_fail()
+    g = lib()
+    A = wl.householder_diag(256, 1e2, seed=9)[0]
+    B = wl.matrix_normal(256, 3, seed=10)
+    with g.Server(4 << 30, max_slots=1) as srv:
+        t = srv.enqueue(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())
+        r = srv.wait([t])[t]
+    assert r["status"] == "done" and r["eta"] <= 1e-12
