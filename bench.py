@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--ref-sample-n", type=int, default=4096,
                     help="order of the matrix the CPU oracle factors in each --impl reference step")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=["lu64", "mixed", "batched"], default="lu64",
+    ap.add_argument("--workload", choices=["lu64", "mixed", "batched", "serving"], default="lu64",
                     help="lu64: the FP64 factorization (default line); mixed: only the mixed-precision "
                          "refinement measurement")
     ap.add_argument("--mixed-n", type=int, default=32768)
@@ -309,6 +309,75 @@ def run_batched(a, dev, count=8192, warmup=2, steps=3):
 
 
 # ---------------------------------------------------------------------------
+# serving: Poisson arrivals, n log-uniform [32, 8192], 1-64 rhs,
+# kappa log-uniform [1e1, 1e6], 20% repeat matrix ids, 120 GB budget
+# ---------------------------------------------------------------------------
+def run_serving(a, dev, rate=2000.0, count=400, pool=24, slots=6, budget=120 << 30):
+    import time
+    import torch
+    import paper_2010_05975_gb300 as g
+    import workloads as wl
+    sizes = wl.batch_sizes(pool, 32, 8192, seed=a.seed, stream=31)
+    ku = wl.uniform01(a.seed, 33, np.arange(pool, dtype=np.uint64))
+    kappas = 10.0 ** (1.0 + 5.0 * ku)
+    mats = [householder_on_device(int(n), float(k), 500 + i, dev) for i, (n, k) in enumerate(zip(sizes, kappas))]
+    u = wl.uniform01(a.seed, 35, np.arange(3 * count, dtype=np.uint64)).reshape(3, count)
+    midx = np.minimum(np.floor(u[0] * pool).astype(int), pool - 1)
+    nrhs = 1 + np.minimum(np.floor(u[1] * 64).astype(int), 63)
+    repeat = u[2] < 0.2
+    arrivals = wl.poisson_arrivals(rate, 4.0 * count / rate + 1.0, seed=a.seed)[:count]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(a.seed)
+    Bs = [torch.randn(mats[m].shape[0], int(r), dtype=torch.float64, device=dev, generator=gen)
+          for m, r in zip(midx, nrhs)]
+    torch.cuda.synchronize(dev)
+    out = {"requests": count, "offered_rate": rate, "pool_matrices": pool, "slots": slots,
+           "budget_bytes": budget, "n_range": [32, 8192], "nrhs_range": [1, 64], "kappa_range": [1e1, 1e6],
+           "repeat_fraction": float(repeat.mean())}
+    with g.Server(budget, max_slots=slots) as srv:
+        # warm-up: one request per precision path, not timed
+        wt = [srv.enqueue(mats[i], Bs[0][: mats[i].shape[0]] if Bs[0].shape[0] == mats[i].shape[0] else
+                          torch.ones(mats[i].shape[0], 1, dtype=torch.float64, device=dev), borrow=True)
+              for i in range(min(3, pool))]
+        srv.wait(wt)
+        t0 = time.perf_counter()
+        pending, res, t_last = {}, {}, t0
+        for i in range(count):
+            while time.perf_counter() - t0 < arrivals[i]:
+                time.sleep(0.0002)
+            mid = int(midx[i]) + 1 if repeat[i] else 0
+            pending[srv.enqueue(mats[midx[i]], Bs[i], matrix_id=mid, borrow=True)] = i
+            for t in list(pending)[:8]:
+                r = srv.poll(t)
+                if r["status"] in ("done", "failed"):
+                    res[pending.pop(t)] = r
+                    t_last = time.perf_counter()
+        while pending:
+            for t in list(pending):
+                r = srv.poll(t)
+                if r["status"] in ("done", "failed"):
+                    res[pending.pop(t)] = r
+                    t_last = time.perf_counter()
+            time.sleep(0.0005)
+        st = srv.stats()
+    lat = np.array([r["latency_s"] for r in res.values()])
+    svc = np.array([r["latency_s"] - r["queue_s"] for r in res.values()])
+    ok = [r for r in res.values() if r["status"] == "done"]
+    out.update({"completed": len(ok), "failed": count - len(ok),
+                "solves_per_s": len(ok) / (t_last - t0), "wall_s": t_last - t0,
+                "p50_latency_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_latency_ms": 1e3 * float(np.percentile(lat, 99)),
+                "p50_service_ms": 1e3 * float(np.percentile(svc, 50)),
+                "p99_service_ms": 1e3 * float(np.percentile(svc, 99)),
+                "max_eta": float(max(r["eta"] for r in ok)) if ok else None,
+                "cache_hits": int(sum(r["cache_hit"] for r in ok)),
+                "peak_bytes": int(st["peak_bytes"]), "peak_running": int(st["peak_running"])})
+    del mats, Bs
+    torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
 def traffic_per_launch(avg_flops_per_launch: float):
@@ -431,11 +500,13 @@ def run_ours(a):
     shares = {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof.items()}
     mixed = None
     batched = None
+    serving = None
     if not a.no_mixed and world == 1:
         del dA0, dA
         torch.cuda.empty_cache()
         mixed = run_mixed(a, dev, t_fp64_factor=tmax / a.steps)
         batched = run_batched(a, dev)
+        serving = run_serving(a, dev)
 
     if rank != 0:
         if world > 1:
@@ -452,7 +523,8 @@ def run_ours(a):
            "warmup": a.warmup, "ms_per_step": 1e3 * tmax / a.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": cfg, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
-           "gpu_launches": launches, "kernel_time_ms": shares, "mixed_ir": mixed, "batched": batched}
+           "gpu_launches": launches, "kernel_time_ms": shares, "mixed_ir": mixed, "batched": batched,
+           "serving": serving}
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -462,7 +534,7 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    elif a.workload in ("mixed", "batched"):
+    elif a.workload in ("mixed", "batched", "serving"):
         import torch
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
         torch.cuda.set_device(dev)
@@ -471,9 +543,12 @@ def main():
         if a.workload == "mixed":
             print(json.dumps({"metric": "IR solves/s at 1e-12 backward error", "unit": "solves/s",
                               "mixed_ir": run_mixed(a, dev)}), flush=True)
-        else:
+        elif a.workload == "batched":
             print(json.dumps({"metric": "batched LU matrices/s", "unit": "matrices/s",
                               "batched": run_batched(a, dev)}), flush=True)
+        else:
+            print(json.dumps({"metric": "IR solves/s & p99 latency at 1e-12 bwd err", "unit": "solves/s",
+                              "serving": run_serving(a, dev)}), flush=True)
     else:
         run_ours(a)
 

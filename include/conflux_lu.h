@@ -255,6 +255,9 @@ int ir_solve(int n, int nrhs, const double *A, int lda, const double *B,
 #define SERVE_DONE      2
 #define SERVE_FAILED    3
 #define SERVE_FLAG_FAIL 1       /* dry-run only: the request reports failure */
+#define SERVE_FLAG_BORROW 2     /* read A and B in place instead of copying them
+                                   at enqueue; the caller keeps them unchanged
+                                   until the ticket is retired by serve_poll   */
 
 typedef struct serve_t serve_t;
 
@@ -308,7 +311,8 @@ typedef struct {
 int serve_create(const serve_cfg *cfg, serve_t **h);
 /* Copy a request and queue it.  Returns 0 with *ticket set, -2 for bad
  * request fields, LU_EBUSY when it can never fit the budget, the queue is
- * full or the server is stopping.  The caller may free A and B on return. */
+ * full or the server is stopping.  The caller may free A and B on return,
+ * unless the request carries SERVE_FLAG_BORROW. */
 int serve_enqueue(serve_t *h, const serve_req *r, uint64_t *ticket);
 /* Non-blocking.  Fills st; once st->status is SERVE_DONE the solution is
  * copied to X (host, n x nrhs row-major, may be NULL) and the ticket is

@@ -75,6 +75,7 @@ class serve_stats(ctypes.Structure):
 
 SERVE_PENDING, SERVE_RUNNING, SERVE_DONE, SERVE_FAILED = 0, 1, 2, 3
 SERVE_FLAG_FAIL = 1
+SERVE_FLAG_BORROW = 2
 
 
 class lu_prof_entry(ctypes.Structure):

@@ -40,6 +40,10 @@ struct Req {
     uint64_t matrix_id = 0;
     double tol = 1e-12;
     std::vector<double> A, B, X;
+    bool borrow = false, dev_in = false;     // borrow: read the caller's buffers in place
+    const double* bA = nullptr;
+    const double* bB = nullptr;
+    int blda = 0, bldb = 0;
     int status = SERVE_PENDING;
     int error = 0;
     int cache_hit = 0;
@@ -143,21 +147,31 @@ int Server::enqueue(const serve_req& q, uint64_t* ticket) {
     r->persistent = persistent_bytes(q.n);
     r->transient = transient_bytes(q.n, q.nrhs);
     if (r->persistent + r->transient > cfg_.hbm_budget_bytes) return LU_EBUSY;   // can never fit
-    r->A.resize(static_cast<size_t>(q.n) * q.n);
-    r->B.resize(static_cast<size_t>(q.n) * q.nrhs);
-    if (q.device_inputs && !cfg_.dry_run) {
-        if (cudaMemcpy2D(r->A.data(), sizeof(double) * q.n, q.A, sizeof(double) * q.lda, sizeof(double) * q.n, q.n,
-                         cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy2D(r->B.data(), sizeof(double) * q.nrhs, q.B, sizeof(double) * q.ldb, sizeof(double) * q.nrhs,
-                         q.n, cudaMemcpyDeviceToHost) != cudaSuccess) {
-            cudaGetLastError();
-            return LU_ELAUNCH;
-        }
-    } else if (!q.device_inputs) {
-        for (int i = 0; i < q.n; ++i) {
-            std::memcpy(&r->A[static_cast<size_t>(i) * q.n], q.A + static_cast<size_t>(i) * q.lda, sizeof(double) * q.n);
-            std::memcpy(&r->B[static_cast<size_t>(i) * q.nrhs], q.B + static_cast<size_t>(i) * q.ldb,
-                        sizeof(double) * q.nrhs);
+    r->borrow = (q.flags & SERVE_FLAG_BORROW) != 0;
+    r->dev_in = q.device_inputs != 0;
+    if (r->borrow) {
+        r->bA = q.A;
+        r->bB = q.B;
+        r->blda = q.lda;
+        r->bldb = q.ldb;
+    } else {
+        r->A.resize(static_cast<size_t>(q.n) * q.n);
+        r->B.resize(static_cast<size_t>(q.n) * q.nrhs);
+        if (q.device_inputs && !cfg_.dry_run) {
+            if (cudaMemcpy2D(r->A.data(), sizeof(double) * q.n, q.A, sizeof(double) * q.lda, sizeof(double) * q.n,
+                             q.n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                cudaMemcpy2D(r->B.data(), sizeof(double) * q.nrhs, q.B, sizeof(double) * q.ldb,
+                             sizeof(double) * q.nrhs, q.n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                cudaGetLastError();
+                return LU_ELAUNCH;
+            }
+        } else if (!q.device_inputs) {
+            for (int i = 0; i < q.n; ++i) {
+                std::memcpy(&r->A[static_cast<size_t>(i) * q.n], q.A + static_cast<size_t>(i) * q.lda,
+                            sizeof(double) * q.n);
+                std::memcpy(&r->B[static_cast<size_t>(i) * q.nrhs], q.B + static_cast<size_t>(i) * q.ldb,
+                            sizeof(double) * q.nrhs);
+            }
         }
     }
     r->t_enq = Clock::now();
@@ -312,21 +326,40 @@ void Server::run(Req* r, cudaStream_t s) {
         fac = hit->fac;
     }
     const size_t nn = static_cast<size_t>(n) * n;
+    const cudaMemcpyKind kin = r->dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const double* Ause = A64;
+    int ldu = n;
     if (!hit) {
-        if (cudaMallocAsync(reinterpret_cast<void**>(&A64), nn * sizeof(double), s) != cudaSuccess) rc = LU_ENOMEM;
-        if (!rc && cudaMemcpyAsync(A64, r->A.data(), nn * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
-            rc = LU_ELAUNCH;
+        if (r->borrow && r->dev_in) {
+            Ause = r->bA;                                     // the caller's device matrix, read in place
+            ldu = r->blda;
+        } else {
+            if (cudaMallocAsync(reinterpret_cast<void**>(&A64), nn * sizeof(double), s) != cudaSuccess) rc = LU_ENOMEM;
+            if (!rc) {
+                const cudaError_t e =
+                    r->borrow ? cudaMemcpy2DAsync(A64, sizeof(double) * n, r->bA, sizeof(double) * r->blda,
+                                                  sizeof(double) * n, n, kin, s)
+                              : cudaMemcpyAsync(A64, r->A.data(), nn * sizeof(double), cudaMemcpyHostToDevice, s);
+                if (e != cudaSuccess) rc = LU_ELAUNCH;
+            }
+            Ause = A64;
+        }
     }
     if (!rc && (cudaMallocAsync(reinterpret_cast<void**>(&B64), sizeof(double) * n * nr, s) != cudaSuccess ||
                 cudaMallocAsync(reinterpret_cast<void**>(&X64), sizeof(double) * n * nr, s) != cudaSuccess))
         rc = LU_ENOMEM;
-    if (!rc && cudaMemcpyAsync(B64, r->B.data(), sizeof(double) * n * nr, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        rc = LU_ELAUNCH;
-    if (!rc && !hit) rc = ir_factor(n, A64, n, r->precision, 128, 128, &fac, s);
+    if (!rc) {
+        const cudaError_t e =
+            r->borrow ? cudaMemcpy2DAsync(B64, sizeof(double) * nr, r->bB, sizeof(double) * r->bldb,
+                                          sizeof(double) * nr, n, kin, s)
+                      : cudaMemcpyAsync(B64, r->B.data(), sizeof(double) * n * nr, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) rc = LU_ELAUNCH;
+    }
+    if (!rc && !hit) rc = ir_factor(n, Ause, ldu, r->precision, 128, 128, &fac, s);
     ir_opts o{};
     o.precision = r->precision;
     o.tol = r->tol;
-    if (!rc) rc = ir_refine(&fac, A64, n, nr, B64, nr, X64, nr, &o, &r->res, s);
+    if (!rc) rc = ir_refine(&fac, Ause, ldu, nr, B64, nr, X64, nr, &o, &r->res, s);
     if (!rc) {
         r->X.resize(static_cast<size_t>(n) * nr);
         if (cudaMemcpyAsync(r->X.data(), X64, sizeof(double) * n * nr, cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -346,7 +379,16 @@ void Server::run(Req* r, cudaStream_t s) {
         hit->last_use = ++clock_;
         return;
     }
-    const bool keep = ok && r->matrix_id != 0 && cache_.find(r->matrix_id) == cache_.end();
+    bool keep = ok && r->matrix_id != 0 && cache_.find(r->matrix_id) == cache_.end();
+    if (keep && A64 == nullptr) {
+        // a borrowed device matrix: the cache keeps its own copy
+        if (cudaMallocAsync(reinterpret_cast<void**>(&A64), nn * sizeof(double), s) != cudaSuccess ||
+            cudaMemcpy2DAsync(A64, sizeof(double) * n, Ause, sizeof(double) * ldu, sizeof(double) * n, n,
+                              cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            cudaGetLastError();
+            keep = false;
+        }
+    }
     if (keep) {
         Entry e;
         e.id = r->matrix_id;

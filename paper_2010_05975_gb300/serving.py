@@ -23,10 +23,16 @@ class Server:
         nat.check("serve_create", self._lib.serve_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
         self._shapes = {}
+        self._borrowed = {}
 
-    def enqueue(self, A, B, matrix_id: int = 0, tol: float = 0.0, precision: int = 0, flags: int = 0) -> int:
+    def enqueue(self, A, B, matrix_id: int = 0, tol: float = 0.0, precision: int = 0, flags: int = 0,
+                borrow: bool = False) -> int:
         """Queue A X = B.  A, B: float64 numpy arrays (host) or CUDA tensors.
+        borrow=True: the server reads A and B in place (no copy at enqueue);
+        this object keeps them referenced until the ticket is retired.
         Returns the ticket.  Raises LuError (LU_EBUSY when it cannot fit)."""
+        if borrow:
+            flags |= nat.SERVE_FLAG_BORROW
         keep = []
         if hasattr(A, "is_cuda") and A.is_cuda:
             dev_in = 1
@@ -43,9 +49,10 @@ class Server:
         req = nat.serve_req(n, nr, pa, lda, pb, ldb, dev_in, int(matrix_id), float(tol), int(precision), int(flags))
         t = ctypes.c_uint64(0)
         rc = self._lib.serve_enqueue(self._h, ctypes.byref(req), ctypes.byref(t))
-        del keep
         nat.check("serve_enqueue", rc)
         self._shapes[t.value] = (n, nr)
+        if borrow:
+            self._borrowed[t.value] = (A, B2, keep)
         return t.value
 
     def poll(self, ticket: int):
@@ -61,6 +68,7 @@ class Server:
                "precision": st.precision, "cache_hit": st.cache_hit}
         if st.status in (nat.SERVE_DONE, nat.SERVE_FAILED):
             self._shapes.pop(ticket, None)
+            self._borrowed.pop(ticket, None)
             if st.status == nat.SERVE_DONE:
                 out["X"] = X
         return out

@@ -85,3 +85,19 @@ def test_device_inputs():
         t = srv.enqueue(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())
         r = srv.wait([t])[t]
     assert r["status"] == "done" and r["eta"] <= 1e-12
+
+
+def test_borrowed_inputs_match_copied():
+    """SERVE_FLAG_BORROW reads the caller's buffers in place; same X as a copy."""
+    torch = cuda_or_fail()
+    g = lib()
+    A = wl.householder_diag(500, 1e3, seed=21)[0]
+    B = wl.matrix_normal(500, 5, seed=22)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    with g.Server(4 << 30, max_slots=2) as srv:
+        t1 = srv.enqueue(A, B)
+        t2 = srv.enqueue(dA, dB, borrow=True)
+        t3 = srv.enqueue(A, B, borrow=True)
+        res = srv.wait([t1, t2, t3])
+    np.testing.assert_array_equal(res[t1]["X"], res[t2]["X"])
+    np.testing.assert_array_equal(res[t1]["X"], res[t3]["X"])
