@@ -390,7 +390,6 @@ def traffic_per_launch(avg_flops_per_launch: float):
     try:
         rec = json.load(open(path)).get("schur_f64")
         src = open(os.path.join(ROOT, "paper_2010_05975_gb300", "csrc", "schur_f64.cu"), "rb").read()
-        src += open(os.path.join(ROOT, "paper_2010_05975_gb300", "csrc", "common.cuh"), "rb").read()
         if not rec or rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
             return None
         return rec["dram_bytes_per_flop"] * avg_flops_per_launch
