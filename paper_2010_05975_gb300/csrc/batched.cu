@@ -8,6 +8,7 @@
 // index ascending, IEEE division), so each matrix's factors equal the
 // oracle's for the same panel width and leaf height.
 #include "common.cuh"
+#include "node_gepp.cuh"
 #include "prof.cuh"
 #include <climits>
 
@@ -26,24 +27,19 @@ __host__ __device__ inline int panel_width(int n) { return n <= 256 ? 16 : 32; }
 
 template <typename T>
 struct Smem {
-    T W[kRMax * (kMaxB + 1)];                    // node rows (GEPP); reused by the phases below
+    alignas(16) T W[kRMax * gepp_ws<T>(kMaxB)];  // node rows (GEPP); reused by the phases below
     T a00[kMaxB * kMaxB];                        // root's factored rows, pivot order
     int ids[kRMax];
     int ord[kRMax];
     int lists[2][kMaxNodes * kMaxB];
     int cnts[2][kMaxNodes];
     int win[kMaxB];
+    int lrow[kMaxB];
     int mv[1 + 4 * kMaxB];
-    T pv[2][32];
-    int pp[2][32], pl[2][32];
+    GeppSlots<T> gs;
     int zero_first;
     int next;
 };
-
-template <typename T>
-__device__ __forceinline__ bool better(T v1, int p1, T v2, int p2) {
-    return v1 > v2 || (v1 == v2 && p1 < p2);
-}
 
 // GEPP selection on the node's rows (a contiguous range or a list), panel
 // columns [k, k+w).  Writes min(nr, w) row positions in pivot order to out;
@@ -52,98 +48,29 @@ __device__ __forceinline__ bool better(T v1, int p1, T v2, int p2) {
 template <typename T>
 __device__ void node_select(Smem<T>& sm, const T* A, int lda, int k, int w, int nr, int r0, const int* list,
                             int* out, bool root) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    const int ws = w + 1;
+    const int tid = threadIdx.x;
+    const int ws = gepp_ws<T>(w);
     T* W = sm.W;
+    // rows in ascending position order (the blocked GEPP breaks ties by row)
+    if (list) {
+        for (int i = tid; i < nr; i += blockDim.x) {
+            const int pi = list[i];
+            int rank = 0;
+            for (int j = 0; j < nr; ++j) rank += (list[j] < pi) ? 1 : 0;
+            sm.ids[rank] = pi;
+        }
+    } else {
+        for (int r = tid; r < nr; r += blockDim.x) sm.ids[r] = r0 + r;
+    }
+    for (int r = tid; r < nr; r += blockDim.x) sm.ord[r] = -1;
+    __syncthreads();
     for (int e = tid; e < nr * w; e += blockDim.x) {
         const int r = e / w, j = e % w;
-        const int pos = list ? list[r] : r0 + r;
-        W[r * ws + j] = A[idx(pos, k + j, lda)];
-    }
-    for (int r = tid; r < nr; r += blockDim.x) {
-        sm.ids[r] = list ? list[r] : r0 + r;
-        sm.ord[r] = -1;
+        W[r * ws + j] = A[idx(sm.ids[r], k + j, lda)];
     }
     __syncthreads();
-    const int ns = min(nr, w);
-    int tpr = 1;
-    while (tpr < 32 && 2 * tpr * nr <= static_cast<int>(blockDim.x)) tpr *= 2;
-    const int rpp = static_cast<int>(blockDim.x) / tpr;
-    const int jj = tid % tpr;
-    const unsigned gmask = (tpr == 32) ? 0xffffffffu : (((1u << tpr) - 1u) << (lane & ~(tpr - 1)));
-    const int glead = lane & ~(tpr - 1);
-    T bv = T(-1);
-    int bp = INT_MAX, bl = -1;
-    if (jj == 0 && ns > 0)
-        for (int r = tid / tpr; r < nr; r += rpp) {
-            T v = abs(W[r * ws]);
-            if (!(v == v)) v = T(INFINITY);
-            if (better(v, sm.ids[r], bv, bp)) {
-                bv = v;
-                bp = sm.ids[r];
-                bl = r;
-            }
-        }
-    for (int c = 0; c < ns; ++c) {
-        const int buf = c & 1;
-        for (int off = 16; off > 0; off >>= 1) {
-            T ov = __shfl_down_sync(0xffffffffu, bv, off);
-            int op = __shfl_down_sync(0xffffffffu, bp, off);
-            int ol = __shfl_down_sync(0xffffffffu, bl, off);
-            if (better(ov, op, bv, bp)) {
-                bv = ov;
-                bp = op;
-                bl = ol;
-            }
-        }
-        if (lane == 0) {
-            sm.pv[buf][warp] = bv;
-            sm.pp[buf][warp] = bp;
-            sm.pl[buf][warp] = bl;
-        }
-        __syncthreads();
-        T v = sm.pv[buf][0];
-        int p = sm.pp[buf][0], lr = sm.pl[buf][0];
-        for (int i = 1; i < nwarp; ++i)
-            if (better(sm.pv[buf][i], sm.pp[buf][i], v, p)) {
-                v = sm.pv[buf][i];
-                p = sm.pp[buf][i];
-                lr = sm.pl[buf][i];
-            }
-        if (tid == 0) out[c] = p;
-        const T* pr = W + lr * ws;
-        const T pvv = pr[c];
-        if (root && pvv == T(0) && tid == 0 && sm.zero_first < 0) sm.zero_first = c;
-        bv = T(-1);
-        bp = INT_MAX;
-        bl = -1;
-        const bool nxt = (c + 1 < ns);
-        for (int r = tid / tpr; r < nr; r += rpp) {
-            if (r == lr) {
-                if (jj == 0) sm.ord[r] = c;
-                continue;
-            }
-            if (sm.ord[r] >= 0) continue;
-            T* wr = W + r * ws;
-            if (pvv != T(0)) {
-                T l = T(0);
-                if (jj == 0) l = wr[c] / pvv;
-                l = __shfl_sync(gmask, l, glead);
-                if (jj == 0) wr[c] = l;
-                for (int j = c + 1 + jj; j < w; j += tpr) wr[j] = fma(-l, pr[j], wr[j]);
-            }
-            if (nxt && jj == 0) {
-                T vv = abs(wr[c + 1]);
-                if (!(vv == vv)) vv = T(INFINITY);
-                if (better(vv, sm.ids[r], bv, bp)) {
-                    bv = vv;
-                    bp = sm.ids[r];
-                    bl = r;
-                }
-            }
-        }
-    }
-    __syncthreads();
+    node_gepp_blocked<T>(W, ws, nr, w, min(nr, w), sm.ids, sm.ord, out, sm.lrow, sm.gs,
+                         root ? &sm.zero_first : nullptr);
     if (root)
         for (int e = tid; e < nr * w; e += blockDim.x) {
             const int r = e / w, j = e % w;

@@ -35,10 +35,6 @@ static int ws_alloc(FactorWs& ws, int m, int b, int h, size_t elem, cudaStream_t
     return 0;
 }
 
-// Largest dynamic shared memory a tournament CTA may take (the kernel also
-// uses ~1 KB of static shared memory).
-constexpr size_t kTsluSmemLimit = 232448 - 2048;
-
 static bool tslu_shapes_fit(int m, int kmax, int b, int h, int elem) {
     for (int k = 0; k < kmax; k += b) {
         const int w = (kmax - k) < b ? (kmax - k) : b;

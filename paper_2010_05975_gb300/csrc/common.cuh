@@ -64,8 +64,14 @@ struct TsluShape {
     int nr_max;   // most rows any node stacks
     int C;        // CTAs per node (cluster size)
     int R;        // rows per CTA
+    int ws;       // row stride of the node's rows in shared memory (elements)
+    int blocked;  // one-CTA node run by the blocked GEPP (node_gepp.cuh)
     size_t smem;  // dynamic shared memory per CTA (bytes)
 };
+
+// Largest dynamic shared memory a tournament CTA may take (the kernel also
+// uses up to ~6 KB of static shared memory).
+constexpr size_t kTsluSmemLimit = 232448 - 8192;
 
 // Leaves of h rows whose selection keeps every row (h <= w) are merged
 // upward until a node holds more than w rows: selection is independent of

@@ -14,6 +14,7 @@
 // nodes keep all their rows, are skipped: the first launched level takes
 // contiguous row ranges of H rows.
 #include "common.cuh"
+#include "node_gepp.cuh"
 #include "prof.cuh"
 #include <cooperative_groups.h>
 #include <climits>
@@ -45,8 +46,16 @@ TsluShape tslu_shape(int m, int k, int w, int h, int max_cluster, int elem) {
     }
     s.C = C;
     s.R = R;
-    s.smem = static_cast<size_t>(R) * (w + 1) * elem + static_cast<size_t>(w) * elem +
-             static_cast<size_t>(R) * 2 * sizeof(int) + static_cast<size_t>(w) * sizeof(int);
+    auto bytes = [&](int ws) {
+        return static_cast<size_t>(R) * ws * elem + static_cast<size_t>(w) * elem +
+               static_cast<size_t>(R) * 2 * sizeof(int) + static_cast<size_t>(2 * w) * sizeof(int);
+    };
+    // A node on one CTA whose rows fit one per thread runs the blocked GEPP.
+    const int threads = (elem == 4) ? 512 : kTsluThreads;
+    const int bws = (elem == 8) ? gepp_ws<double>(w) : gepp_ws<float>(w);
+    s.blocked = (C == 1 && R <= threads && bytes(bws) <= kTsluSmemLimit) ? 1 : 0;
+    s.ws = s.blocked ? bws : w + 1;
+    s.smem = bytes(s.ws);
     return s;
 }
 
@@ -65,6 +74,8 @@ struct LevelArgs {
     T* a00;             // root: w x w rows of the factored winners, pivot order
     int* info;          // root: first zero pivot
     int C, R;
+    int ws;             // row stride of W
+    int blocked;        // one-CTA node: blocked GEPP
 };
 
 template <typename T>
@@ -90,14 +101,17 @@ __device__ __forceinline__ void warp_argmax(T& v, int& p, int& l) {
 template <typename T>
 constexpr int tslu_threads() { return sizeof(T) == 4 ? 512 : kTsluThreads; }
 
-template <typename T>
+// BLOCKED: one-CTA nodes run the blocked GEPP; otherwise the column-by-column
+// GEPP over a cluster.  Two instantiations, so that each keeps its own
+// register allocation.
+template <typename T, bool BLOCKED>
 __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs<T> a) {
     cg::cluster_group cluster = cg::this_cluster();
     const int q = static_cast<int>(cluster.block_rank());
     const int node = blockIdx.x / a.C;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarp = blockDim.x >> 5;
-    const int w = a.w, ws = w + 1;
+    const int w = a.w, ws = a.ws;
 
     int nr, r0 = 0, cl = 0;
     const int* lp = nullptr;
@@ -133,6 +147,7 @@ __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs
     int* ids = reinterpret_cast<int*>(prow + w);          // R
     int* ord = ids + a.R;                                 // R
     int* winp = ord + a.R;                                // w
+    int* lrow = winp + w;                                 // w (blocked GEPP)
     __shared__ T slot_v[2];
     __shared__ int slot_p[2], slot_l[2];
     __shared__ T part_v[2][32];
@@ -141,9 +156,22 @@ __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs
 
     const int i0 = q * a.R;
     const int nloc = max(0, min(a.R, nr - i0));
+    if (BLOCKED && a.level > 0) {
+        // The blocked GEPP breaks ties by row: stack the candidates in
+        // ascending position order (the selection does not depend on it).
+        for (int i = tid; i < nr; i += blockDim.x) ord[i] = (i < cl) ? lp[i] : rp[i - cl];
+        __syncthreads();
+        for (int i = tid; i < nr; i += blockDim.x) {
+            const int pi = ord[i];
+            int rank = 0;
+            for (int j = 0; j < nr; ++j) rank += (ord[j] < pi) ? 1 : 0;
+            ids[rank] = pi;
+        }
+        __syncthreads();
+    }
     for (int r = warp; r < nloc; r += nwarp) {
         const int gi = i0 + r;
-        const int pos = (a.level == 0) ? (r0 + gi) : (gi < cl ? lp[gi] : rp[gi - cl]);
+        const int pos = (a.level == 0) ? (r0 + gi) : BLOCKED ? ids[r] : (gi < cl ? lp[gi] : rp[gi - cl]);
         if (lane == 0) {
             ids[r] = pos;
             ord[r] = -1;
@@ -155,139 +183,144 @@ __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs
     __syncthreads();
 
     const int ns = min(nr, w);
-    // Row groups: tpr (a power of two <= 32) threads per row, all in one warp.
-    int tpr = 1;
-    while (tpr < 32 && 2 * tpr * max(nloc, 1) <= static_cast<int>(blockDim.x)) tpr *= 2;
-    const int rows_per_pass = static_cast<int>(blockDim.x) / tpr;
-    const int jj = tid % tpr;
-    const unsigned gmask = (tpr == 32) ? 0xffffffffu : (((1u << tpr) - 1u) << (lane & ~(tpr - 1)));
-    const int glead = lane & ~(tpr - 1);
+    if constexpr (BLOCKED) {
+        __shared__ GeppSlots<T> gslots;
+        node_gepp_blocked<T>(W, ws, nloc, w, ns, ids, ord, winp, lrow, gslots, &s_zero);
+    } else {
+        // Row groups: tpr (a power of two <= 32) threads per row, all in one warp.
+        int tpr = 1;
+        while (tpr < 32 && 2 * tpr * max(nloc, 1) <= static_cast<int>(blockDim.x)) tpr *= 2;
+        const int rows_per_pass = static_cast<int>(blockDim.x) / tpr;
+        const int jj = tid % tpr;
+        const unsigned gmask = (tpr == 32) ? 0xffffffffu : (((1u << tpr) - 1u) << (lane & ~(tpr - 1)));
+        const int glead = lane & ~(tpr - 1);
 
-    // candidate of column 0 (later columns come out of the fused update)
-    T bv = T(-1);
-    int bp = INT_MAX, bl = -1;
-    if (jj == 0 && ns > 0)
-        for (int r = tid / tpr; r < nloc; r += rows_per_pass) {
-            T v = abs(W[r * ws + 0]);
-            if (!(v == v)) v = T(INFINITY);     // a NaN row still wins: the step always has a pivot row
-            if (better(v, ids[r], bv, bp)) {
-                bv = v;
-                bp = ids[r];
-                bl = r;
-            }
-        }
-    for (int c = 0; c < ns; ++c) {
-        // 1. per-warp argmax of the candidates for column c (double-buffered
-        //    partials: a warp may run one step ahead of a slow reader)
-        const int buf = c & 1;
-        warp_argmax(bv, bp, bl);
-        if (lane == 0) {
-            part_v[buf][warp] = bv;
-            part_p[buf][warp] = bp;
-            part_l[buf][warp] = bl;
-        }
-        __syncthreads();
-        int lr, owner;
-        if (a.C == 1) {
-            // one-CTA node: every thread folds the partials itself
-            T v = part_v[buf][0];
-            int p = part_p[buf][0], l = part_l[buf][0];
-            for (int i = 1; i < nwarp; ++i)
-                if (better(part_v[buf][i], part_p[buf][i], v, p)) {
-                    v = part_v[buf][i];
-                    p = part_p[buf][i];
-                    l = part_l[buf][i];
-                }
-            lr = l;
-            owner = 0;
-            if (tid == 0) winp[c] = p;
-        } else {
-            if (warp == 0) {
-                bv = lane < nwarp ? part_v[buf][lane] : T(-1);
-                bp = lane < nwarp ? part_p[buf][lane] : INT_MAX;
-                bl = lane < nwarp ? part_l[buf][lane] : -1;
-                warp_argmax(bv, bp, bl);
-                if (lane == 0) {
-                    slot_v[buf] = bv;
-                    slot_p[buf] = bp;
-                    slot_l[buf] = bl;
-                }
-            }
-            cluster.sync();
-            // 2. cluster-wide winner, identical in every CTA
-            if (warp == 0) {
-                T v = T(-1);
-                int p = INT_MAX, l = -1;
-                if (lane < a.C) {
-                    v = cluster.map_shared_rank(slot_v, lane)[buf];
-                    p = cluster.map_shared_rank(slot_p, lane)[buf];
-                    l = cluster.map_shared_rank(slot_l, lane)[buf];
-                }
-                int o = (lane < a.C) ? lane : -1;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    T ov = __shfl_down_sync(0xffffffffu, v, off);
-                    int op = __shfl_down_sync(0xffffffffu, p, off);
-                    int ol = __shfl_down_sync(0xffffffffu, l, off);
-                    int oo = __shfl_down_sync(0xffffffffu, o, off);
-                    if (better(ov, op, v, p)) {
-                        v = ov;
-                        p = op;
-                        l = ol;
-                        o = oo;
-                    }
-                }
-                if (lane == 0) {
-                    s_owner = o;
-                    s_lr = l;
-                    winp[c] = p;
-                    if (o == q) ord[l] = c;
-                }
-            }
-            __syncthreads();
-            owner = s_owner;
-            lr = s_lr;
-        }
-        // 3. the pivot row (never written again): in place for a one-CTA node,
-        //    else copied from the owner's shared memory
-        const T* pr;
-        if (a.C == 1) {
-            pr = W + lr * ws;
-        } else {
-            const T* rW = cluster.map_shared_rank(W, owner);
-            for (int j = c + tid; j < w; j += blockDim.x) prow[j] = rW[lr * ws + j];
-            __syncthreads();
-            pr = prow;
-        }
-        const T pv = pr[c];
-        if (pv == T(0) && tid == 0 && s_zero < 0) s_zero = c;
-        // 4. fused: multiplier (one division per row, shuffled to the row's
-        //    threads), rank-1 update, and the candidate for column c+1.
-        bv = T(-1);
-        bp = INT_MAX;
-        bl = -1;
-        const bool next = (c + 1 < ns);
-        for (int r = tid / tpr; r < nloc; r += rows_per_pass) {
-            if (a.C == 1 && r == lr) {                       // chosen now: mark it, leave it
-                if (jj == 0) ord[r] = c;
-                continue;
-            }
-            if (ord[r] >= 0) continue;                       // uniform over the row's threads
-            T* wr = W + r * ws;
-            if (pv != T(0)) {
-                T l = T(0);
-                if (jj == 0) l = wr[c] / pv;
-                l = __shfl_sync(gmask, l, glead);
-                if (jj == 0) wr[c] = l;
-                for (int j = c + 1 + jj; j < w; j += tpr) wr[j] = fma(-l, pr[j], wr[j]);
-            }
-            if (next && jj == 0) {
-                T v = abs(wr[c + 1]);
-                if (!(v == v)) v = T(INFINITY);
+        // candidate of column 0 (later columns come out of the fused update)
+        T bv = T(-1);
+        int bp = INT_MAX, bl = -1;
+        if (jj == 0 && ns > 0)
+            for (int r = tid / tpr; r < nloc; r += rows_per_pass) {
+                T v = abs(W[r * ws + 0]);
+                if (!(v == v)) v = T(INFINITY);     // a NaN row still wins: the step always has a pivot row
                 if (better(v, ids[r], bv, bp)) {
                     bv = v;
                     bp = ids[r];
                     bl = r;
+                }
+            }
+        for (int c = 0; c < ns; ++c) {
+            // 1. per-warp argmax of the candidates for column c (double-buffered
+            //    partials: a warp may run one step ahead of a slow reader)
+            const int buf = c & 1;
+            warp_argmax(bv, bp, bl);
+            if (lane == 0) {
+                part_v[buf][warp] = bv;
+                part_p[buf][warp] = bp;
+                part_l[buf][warp] = bl;
+            }
+            __syncthreads();
+            int lr, owner;
+            if (a.C == 1) {
+                // one-CTA node: every thread folds the partials itself
+                T v = part_v[buf][0];
+                int p = part_p[buf][0], l = part_l[buf][0];
+                for (int i = 1; i < nwarp; ++i)
+                    if (better(part_v[buf][i], part_p[buf][i], v, p)) {
+                        v = part_v[buf][i];
+                        p = part_p[buf][i];
+                        l = part_l[buf][i];
+                    }
+                lr = l;
+                owner = 0;
+                if (tid == 0) winp[c] = p;
+            } else {
+                if (warp == 0) {
+                    bv = lane < nwarp ? part_v[buf][lane] : T(-1);
+                    bp = lane < nwarp ? part_p[buf][lane] : INT_MAX;
+                    bl = lane < nwarp ? part_l[buf][lane] : -1;
+                    warp_argmax(bv, bp, bl);
+                    if (lane == 0) {
+                        slot_v[buf] = bv;
+                        slot_p[buf] = bp;
+                        slot_l[buf] = bl;
+                    }
+                }
+                cluster.sync();
+                // 2. cluster-wide winner, identical in every CTA
+                if (warp == 0) {
+                    T v = T(-1);
+                    int p = INT_MAX, l = -1;
+                    if (lane < a.C) {
+                        v = cluster.map_shared_rank(slot_v, lane)[buf];
+                        p = cluster.map_shared_rank(slot_p, lane)[buf];
+                        l = cluster.map_shared_rank(slot_l, lane)[buf];
+                    }
+                    int o = (lane < a.C) ? lane : -1;
+    #pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        T ov = __shfl_down_sync(0xffffffffu, v, off);
+                        int op = __shfl_down_sync(0xffffffffu, p, off);
+                        int ol = __shfl_down_sync(0xffffffffu, l, off);
+                        int oo = __shfl_down_sync(0xffffffffu, o, off);
+                        if (better(ov, op, v, p)) {
+                            v = ov;
+                            p = op;
+                            l = ol;
+                            o = oo;
+                        }
+                    }
+                    if (lane == 0) {
+                        s_owner = o;
+                        s_lr = l;
+                        winp[c] = p;
+                        if (o == q) ord[l] = c;
+                    }
+                }
+                __syncthreads();
+                owner = s_owner;
+                lr = s_lr;
+            }
+            // 3. the pivot row (never written again): in place for a one-CTA node,
+            //    else copied from the owner's shared memory
+            const T* pr;
+            if (a.C == 1) {
+                pr = W + lr * ws;
+            } else {
+                const T* rW = cluster.map_shared_rank(W, owner);
+                for (int j = c + tid; j < w; j += blockDim.x) prow[j] = rW[lr * ws + j];
+                __syncthreads();
+                pr = prow;
+            }
+            const T pv = pr[c];
+            if (pv == T(0) && tid == 0 && s_zero < 0) s_zero = c;
+            // 4. fused: multiplier (one division per row, shuffled to the row's
+            //    threads), rank-1 update, and the candidate for column c+1.
+            bv = T(-1);
+            bp = INT_MAX;
+            bl = -1;
+            const bool next = (c + 1 < ns);
+            for (int r = tid / tpr; r < nloc; r += rows_per_pass) {
+                if (a.C == 1 && r == lr) {                       // chosen now: mark it, leave it
+                    if (jj == 0) ord[r] = c;
+                    continue;
+                }
+                if (ord[r] >= 0) continue;                       // uniform over the row's threads
+                T* wr = W + r * ws;
+                if (pv != T(0)) {
+                    T l = T(0);
+                    if (jj == 0) l = wr[c] / pv;
+                    l = __shfl_sync(gmask, l, glead);
+                    if (jj == 0) wr[c] = l;
+                    for (int j = c + 1 + jj; j < w; j += tpr) wr[j] = fma(-l, pr[j], wr[j]);
+                }
+                if (next && jj == 0) {
+                    T v = abs(wr[c + 1]);
+                    if (!(v == v)) v = T(INFINITY);
+                    if (better(v, ids[r], bv, bp)) {
+                        bv = v;
+                        bp = ids[r];
+                        bl = r;
+                    }
                 }
             }
         }
@@ -324,7 +357,10 @@ static int launch_level(const LevelArgs<T>& args, int nnode, int C, size_t smem,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     ProfScope ps(LU_PROF_TSLU, s);
-    LU_TRY(cudaLaunchKernelEx(&cfg, tslu_level_kernel<T>, args));
+    if (args.blocked)
+        LU_TRY(cudaLaunchKernelEx(&cfg, tslu_level_kernel<T, true>, args));
+    else
+        LU_TRY(cudaLaunchKernelEx(&cfg, tslu_level_kernel<T, false>, args));
     count_launches(1);
     return 0;
 }
@@ -336,12 +372,12 @@ int tslu_max_cluster() {
     static int cached = kTsluMaxCluster;
     std::call_once(once, [] {
         int best = kTsluMaxCluster;
-        if (cudaFuncSetAttribute(tslu_level_kernel<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                cudaSuccess &&
-            cudaFuncSetAttribute(tslu_level_kernel<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                cudaSuccess) {
+        if (cudaFuncSetAttribute(tslu_level_kernel<double, false>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                 1) == cudaSuccess &&
+            cudaFuncSetAttribute(tslu_level_kernel<float, false>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                 1) == cudaSuccess) {
             const TsluShape sh = tslu_shape(2 * kMaxPanel * 16, 0, kMaxPanel, 128, 16, sizeof(double));
-            if (smem_attr(tslu_level_kernel<double>, sh.smem) == 0) {
+            if (smem_attr(tslu_level_kernel<double, false>, sh.smem) == 0) {
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3(16);
                 cfg.blockDim = dim3(kTsluThreads);
@@ -354,7 +390,7 @@ int tslu_max_cluster() {
                 cfg.attrs = attr;
                 cfg.numAttrs = 1;
                 int nclusters = 0;
-                if (cudaOccupancyMaxActiveClusters(&nclusters, tslu_level_kernel<double>, &cfg) == cudaSuccess &&
+                if (cudaOccupancyMaxActiveClusters(&nclusters, tslu_level_kernel<double, false>, &cfg) == cudaSuccess &&
                     nclusters > 0)
                     best = 16;
             }
@@ -369,7 +405,9 @@ template <typename T>
 int tslu_select(const T* A, int lda, int m, int k, int w, int h, int* lists, int* counts,
                 size_t list_stride_nodes, T* a00, int* info, const int** root_list, cudaStream_t s) {
     const TsluShape sh = tslu_shape(m, k, w, h, tslu_max_cluster(), sizeof(T));
-    if (int rc_ = smem_attr(tslu_level_kernel<T>, sh.smem)) return rc_;
+    if (int rc_ = sh.blocked ? smem_attr(tslu_level_kernel<T, true>, sh.smem)
+                             : smem_attr(tslu_level_kernel<T, false>, sh.smem))
+        return rc_;
     int* list_buf[2] = {lists, lists + list_stride_nodes * w};
     int* cnt_buf[2] = {counts, counts + list_stride_nodes};
     LevelArgs<T> args{};
@@ -383,6 +421,8 @@ int tslu_select(const T* A, int lda, int m, int k, int w, int h, int* lists, int
     args.info = info;
     args.C = sh.C;
     args.R = sh.R;
+    args.ws = sh.ws;
+    args.blocked = sh.blocked;
 
     int nn = sh.nsuper, cur = 0;
     args.level = 0;

@@ -35,7 +35,8 @@ def gpu_factor_f32(A32, b, h, prec=1):
     return dA.cpu().numpy(), piv.cpu().numpy()[: min(m, n)], int(info.cpu()[0])
 
 
-@pytest.mark.parametrize("n,b,h", [(64, 16, 8), (300, 32, 128), (513, 64, 64), (1024, 256, 128)])
+@pytest.mark.parametrize("n,b,h", [(64, 16, 8), (300, 32, 128), (513, 64, 64), (1000, 128, 128), (250, 100, 128),
+                                   (1024, 256, 128)])
 def test_f32_factor_bit_exact(oracle_mod, n, b, h):
     """The all-binary32 path keeps the oracle's operation order: pivots and
     factors equal the oracle's binary32 instance bit for bit."""
@@ -44,6 +45,22 @@ def test_f32_factor_bit_exact(oracle_mod, n, b, h):
     LUo, po, io = oracle_mod.lu_factor_f32(A, b=b, h=h)
     np.testing.assert_array_equal(pg, po)
     assert ig == io
+    np.testing.assert_array_equal(LUg, LUo)
+
+
+@pytest.mark.parametrize("n,b,h", [(200, 16, 8), (600, 128, 128), (300, 100, 128)])
+def test_f32_ties_and_zero_pivots(oracle_mod, n, b, h):
+    """Small integers (many equal |a|, so ties fall to the smaller row
+    position) and two zero columns (steps with a zero pivot update nothing)."""
+    u = wl.uniform01(77, n * n, np.arange(n * n, dtype=np.uint64)).reshape(n, n)
+    A = (np.floor(u * 5.0) - 2.0).astype(np.float32)
+    A[:, n // 3] = 0.0
+    A[:, n // 3 + 5] = 0.0
+    LUg, pg, ig = gpu_factor_f32(A, b, h)
+    LUo, po, io = oracle_mod.lu_factor_f32(A, b=b, h=h)
+    np.testing.assert_array_equal(pg, po)
+    assert ig == io
+    assert io > 0
     np.testing.assert_array_equal(LUg, LUo)
 
 
