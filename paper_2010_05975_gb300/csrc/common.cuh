@@ -65,7 +65,7 @@ struct TsluShape {
     int C;        // CTAs per node (cluster size)
     int R;        // rows per CTA
     int ws;       // row stride of the node's rows in shared memory (elements)
-    int blocked;  // one-CTA node run by the blocked GEPP (node_gepp.cuh)
+    int blocked;  // node GEPP: 1 blocked on one CTA, 2 blocked over a cluster, 0 column by column
     size_t smem;  // dynamic shared memory per CTA (bytes)
 };
 

@@ -140,13 +140,14 @@ __device__ __forceinline__ void gepp_bar(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// Row r's trailing columns from j0 (rounded down to 16 bytes; the columns
-// before j0 are written back unchanged): chunks i = s, s+S, ..., two in
-// flight, each taking the panel's KB updates in pivot order.
+// Row r of W: its trailing columns from j0 (rounded down to 16 bytes; the
+// columns before j0 are written back unchanged), chunks i = s, s+S, ...,
+// two in flight, each taking the panel's KB updates in pivot order.  Pivot
+// row q is row rq[q] of Ub (stride us).
 template <typename T, bool FULL>
 __device__ __forceinline__ void gepp_rank_row(T* W, int ws, int r, int s, int S, int j0, int w,
-                                              const T (&mr)[kGeppKB], const int (&rq)[kGeppKB], int kb,
-                                              unsigned zm) {
+                                              const T (&mr)[kGeppKB], const T* Ub, int us,
+                                              const int (&rq)[kGeppKB], int kb, unsigned zm) {
     constexpr int KB = kGeppKB;
     constexpr int V = 16 / sizeof(T);
     const int cb = j0 & ~(V - 1);
@@ -171,7 +172,7 @@ __device__ __forceinline__ void gepp_rank_row(T* W, int ws, int r, int s, int S,
 #pragma unroll
         for (int q = 0; q < KB; ++q) {
             if (FULL || (q < kb && !((zm >> q) & 1u))) {
-                const T* up = W + static_cast<size_t>(rq[q]) * ws;
+                const T* up = Ub + static_cast<size_t>(rq[q]) * us;
                 T ua[V], ub[V];
                 gepp_ld16(up + jA, ua);
                 if (hasB) gepp_ld16(up + jB, ub);
@@ -347,9 +348,9 @@ __device__ void node_gepp_blocked(T* W, int ws, int nr, int w, int ns, const int
             T mr[KB];
             gepp_vload(W + static_cast<size_t>(r) * ws + c0, mr);
             if (kb == KB && zm == 0)
-                gepp_rank_row<T, true>(W, ws, r, s, S, j0, w, mr, rq, kb, zm);
+                gepp_rank_row<T, true>(W, ws, r, s, S, j0, w, mr, W, ws, rq, kb, zm);
             else
-                gepp_rank_row<T, false>(W, ws, r, s, S, j0, w, mr, rq, kb, zm);
+                gepp_rank_row<T, false>(W, ws, r, s, S, j0, w, mr, W, ws, rq, kb, zm);
         }
         __syncthreads();
     }

@@ -15,6 +15,7 @@
 // contiguous row ranges of H rows.
 #include "common.cuh"
 #include "node_gepp.cuh"
+#include "node_gepp_cluster.cuh"
 #include "prof.cuh"
 #include <cooperative_groups.h>
 #include <climits>
@@ -50,11 +51,34 @@ TsluShape tslu_shape(int m, int k, int w, int h, int max_cluster, int elem) {
         return static_cast<size_t>(R) * ws * elem + static_cast<size_t>(w) * elem +
                static_cast<size_t>(R) * 2 * sizeof(int) + static_cast<size_t>(2 * w) * sizeof(int);
     };
-    // A node on one CTA whose rows fit one per thread runs the blocked GEPP.
+    // A node on one CTA whose rows fit one per thread runs the blocked GEPP
+    // (mode 1); a node over a cluster of at most 32 rows per CTA, the
+    // cluster-blocked GEPP (mode 2); anything else, the column-by-column
+    // GEPP over the cluster (mode 0).
     const int threads = (elem == 4) ? 512 : kTsluThreads;
     const int bws = (elem == 8) ? gepp_ws<double>(w) : gepp_ws<float>(w);
-    s.blocked = (C == 1 && R <= threads && bytes(bws) <= kTsluSmemLimit) ? 1 : 0;
-    s.ws = s.blocked ? bws : w + 1;
+    s.blocked = 0;
+    s.ws = w + 1;
+    if (C == 1 && R <= threads && bytes(bws) <= kTsluSmemLimit) {
+        s.blocked = 1;
+        s.ws = bws;
+    } else {
+        int C2 = 2;
+        while (C2 < max_cluster && cdiv(s.nr_max, C2) > 32) C2 *= 2;
+        const int R2 = cdiv(s.nr_max, C2);
+        const size_t b2 = static_cast<size_t>(R2 + kGeppKB) * bws * elem + static_cast<size_t>(w) * elem +
+                          static_cast<size_t>(R2) * 2 * sizeof(int) + static_cast<size_t>(2 * w) * sizeof(int);
+        // (the candidates' positions are sorted in W's space before the rows arrive)
+        const bool sort_fits = static_cast<size_t>(R2) * bws * elem >= static_cast<size_t>(s.nr_max) * sizeof(int);
+        if (R2 <= 32 && b2 <= kTsluSmemLimit && sort_fits) {
+            s.blocked = 2;
+            s.C = C2;
+            s.R = R2;
+            s.ws = bws;
+            s.smem = b2;
+            return s;
+        }
+    }
     s.smem = bytes(s.ws);
     return s;
 }
@@ -75,7 +99,7 @@ struct LevelArgs {
     int* info;          // root: first zero pivot
     int C, R;
     int ws;             // row stride of W
-    int blocked;        // one-CTA node: blocked GEPP
+    int blocked;        // GEPP mode: 1 one-CTA blocked, 2 cluster-blocked, 0 column by column
 };
 
 template <typename T>
@@ -101,10 +125,10 @@ __device__ __forceinline__ void warp_argmax(T& v, int& p, int& l) {
 template <typename T>
 constexpr int tslu_threads() { return sizeof(T) == 4 ? 512 : kTsluThreads; }
 
-// BLOCKED: one-CTA nodes run the blocked GEPP; otherwise the column-by-column
-// GEPP over a cluster.  Two instantiations, so that each keeps its own
-// register allocation.
-template <typename T, bool BLOCKED>
+// MODE 1: one-CTA nodes, blocked GEPP; MODE 2: nodes over a cluster,
+// cluster-blocked GEPP; MODE 0: nodes over a cluster, column-by-column GEPP.
+// Separate instantiations, so that each keeps its own register allocation.
+template <typename T, int MODE>
 __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs<T> a) {
     cg::cluster_group cluster = cg::this_cluster();
     const int q = static_cast<int>(cluster.block_rank());
@@ -143,7 +167,8 @@ __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* W = reinterpret_cast<T*>(smem_raw);              // R x ws
-    T* prow = W + static_cast<size_t>(a.R) * ws;         // w
+    T* Ub = W + static_cast<size_t>(a.R) * ws;           // MODE 2: kGeppKB x ws
+    T* prow = Ub + (MODE == 2 ? static_cast<size_t>(kGeppKB) * ws : 0);   // w
     int* ids = reinterpret_cast<int*>(prow + w);          // R
     int* ord = ids + a.R;                                 // R
     int* winp = ord + a.R;                                // w
@@ -156,22 +181,24 @@ __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs
 
     const int i0 = q * a.R;
     const int nloc = max(0, min(a.R, nr - i0));
-    if (BLOCKED && a.level > 0) {
-        // The blocked GEPP breaks ties by row: stack the candidates in
-        // ascending position order (the selection does not depend on it).
-        for (int i = tid; i < nr; i += blockDim.x) ord[i] = (i < cl) ? lp[i] : rp[i - cl];
+    if (MODE != 0 && a.level > 0) {
+        // The blocked GEPPs break ties by row: stack the candidates in
+        // ascending position order (the selection does not depend on it);
+        // this CTA keeps ranks [i0, i0 + nloc).
+        int* tmp = reinterpret_cast<int*>(W);             // nr positions, before the rows arrive
+        for (int i = tid; i < nr; i += blockDim.x) tmp[i] = (i < cl) ? lp[i] : rp[i - cl];
         __syncthreads();
         for (int i = tid; i < nr; i += blockDim.x) {
-            const int pi = ord[i];
+            const int pi = tmp[i];
             int rank = 0;
-            for (int j = 0; j < nr; ++j) rank += (ord[j] < pi) ? 1 : 0;
-            ids[rank] = pi;
+            for (int j = 0; j < nr; ++j) rank += (tmp[j] < pi) ? 1 : 0;
+            if (rank >= i0 && rank < i0 + nloc) ids[rank - i0] = pi;
         }
         __syncthreads();
     }
     for (int r = warp; r < nloc; r += nwarp) {
         const int gi = i0 + r;
-        const int pos = (a.level == 0) ? (r0 + gi) : BLOCKED ? ids[r] : (gi < cl ? lp[gi] : rp[gi - cl]);
+        const int pos = (a.level == 0) ? (r0 + gi) : (MODE != 0) ? ids[r] : (gi < cl ? lp[gi] : rp[gi - cl]);
         if (lane == 0) {
             ids[r] = pos;
             ord[r] = -1;
@@ -183,9 +210,13 @@ __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs
     __syncthreads();
 
     const int ns = min(nr, w);
-    if constexpr (BLOCKED) {
+    if constexpr (MODE == 1) {
         __shared__ GeppSlots<T> gslots;
         node_gepp_blocked<T>(W, ws, nloc, w, ns, ids, ord, winp, lrow, gslots, &s_zero);
+    } else if constexpr (MODE == 2) {
+        __shared__ GeppClusterSlot<T> cslot;
+        node_gepp_cluster<T>(W, ws, nloc, a.R, a.C, q, w, ns, ids, ord, winp, Ub, cslot, q == 0 ? &s_zero : nullptr,
+                             a.root != 0);
     } else {
         // Row groups: tpr (a power of two <= 32) threads per row, all in one warp.
         int tpr = 1;
@@ -357,10 +388,12 @@ static int launch_level(const LevelArgs<T>& args, int nnode, int C, size_t smem,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     ProfScope ps(LU_PROF_TSLU, s);
-    if (args.blocked)
-        LU_TRY(cudaLaunchKernelEx(&cfg, tslu_level_kernel<T, true>, args));
+    if (args.blocked == 1)
+        LU_TRY(cudaLaunchKernelEx(&cfg, tslu_level_kernel<T, 1>, args));
+    else if (args.blocked == 2)
+        LU_TRY(cudaLaunchKernelEx(&cfg, tslu_level_kernel<T, 2>, args));
     else
-        LU_TRY(cudaLaunchKernelEx(&cfg, tslu_level_kernel<T, false>, args));
+        LU_TRY(cudaLaunchKernelEx(&cfg, tslu_level_kernel<T, 0>, args));
     count_launches(1);
     return 0;
 }
@@ -372,12 +405,18 @@ int tslu_max_cluster() {
     static int cached = kTsluMaxCluster;
     std::call_once(once, [] {
         int best = kTsluMaxCluster;
-        if (cudaFuncSetAttribute(tslu_level_kernel<double, false>, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                                 1) == cudaSuccess &&
-            cudaFuncSetAttribute(tslu_level_kernel<float, false>, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                                 1) == cudaSuccess) {
+        if (cudaFuncSetAttribute(tslu_level_kernel<double, 0>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(tslu_level_kernel<float, 0>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(tslu_level_kernel<double, 2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(tslu_level_kernel<float, 2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess) {
+            // the largest binary64 node over 16 CTAs, in both cluster modes
             const TsluShape sh = tslu_shape(2 * kMaxPanel * 16, 0, kMaxPanel, 128, 16, sizeof(double));
-            if (smem_attr(tslu_level_kernel<double, false>, sh.smem) == 0) {
+            auto fits16 = [&](auto kernel) {
+                if (smem_attr(kernel, sh.smem) != 0) return false;
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3(16);
                 cfg.blockDim = dim3(kTsluThreads);
@@ -390,10 +429,9 @@ int tslu_max_cluster() {
                 cfg.attrs = attr;
                 cfg.numAttrs = 1;
                 int nclusters = 0;
-                if (cudaOccupancyMaxActiveClusters(&nclusters, tslu_level_kernel<double, false>, &cfg) == cudaSuccess &&
-                    nclusters > 0)
-                    best = 16;
-            }
+                return cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg) == cudaSuccess && nclusters > 0;
+            };
+            if (fits16(tslu_level_kernel<double, 0>) && fits16(tslu_level_kernel<double, 2>)) best = 16;
         }
         cudaGetLastError();
         cached = best;
@@ -405,8 +443,9 @@ template <typename T>
 int tslu_select(const T* A, int lda, int m, int k, int w, int h, int* lists, int* counts,
                 size_t list_stride_nodes, T* a00, int* info, const int** root_list, cudaStream_t s) {
     const TsluShape sh = tslu_shape(m, k, w, h, tslu_max_cluster(), sizeof(T));
-    if (int rc_ = sh.blocked ? smem_attr(tslu_level_kernel<T, true>, sh.smem)
-                             : smem_attr(tslu_level_kernel<T, false>, sh.smem))
+    if (int rc_ = sh.blocked == 1   ? smem_attr(tslu_level_kernel<T, 1>, sh.smem)
+                  : sh.blocked == 2 ? smem_attr(tslu_level_kernel<T, 2>, sh.smem)
+                                    : smem_attr(tslu_level_kernel<T, 0>, sh.smem))
         return rc_;
     int* list_buf[2] = {lists, lists + list_stride_nodes * w};
     int* cnt_buf[2] = {counts, counts + list_stride_nodes};

@@ -93,6 +93,23 @@ def test_zero_column_info(oracle_mod):
     np.testing.assert_array_equal(LUg, LUo)
 
 
+@pytest.mark.parametrize("n,b,h", [(700, 256, 128), (300, 64, 16)])
+def test_cluster_nodes_ties_and_zero_pivots(oracle_mod, n, b, h):
+    """Tournament nodes spread over a cluster: small integers (many equal
+    |a|; ties go to the smaller row position) and two zero columns (steps
+    with a zero pivot update nothing) give the oracle's factors exactly."""
+    u = wl.uniform01(91, n * n, np.arange(n * n, dtype=np.uint64)).reshape(n, n)
+    A = np.floor(u * 5.0) - 2.0
+    A[:, n // 3] = 0.0
+    A[:, n // 3 + 5] = 0.0
+    LUg, pg, ig = run_gpu(A, b, h)
+    LUo, po, io = oracle_mod.lu_factor(A, b=b, h=h)
+    np.testing.assert_array_equal(pg, po)
+    assert ig == io
+    assert io > 0
+    np.testing.assert_array_equal(LUg, LUo)
+
+
 def test_permutation_matrix_exact():
     n = 160
     perm = np.argsort(wl.uniform01(9, n, np.arange(n, dtype=np.uint64)))
