@@ -95,6 +95,24 @@ int trsm_u12(T* A, int lda, int n, int k, int w, cudaStream_t s);
 int schur_f64(double* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s);
 int schur_f32(float* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s);
 int getrs_f64(int n, int nrhs, const double* LU, int lda, const int* piv, double* B, int ldb, cudaStream_t s);
+
+// What a solve needs besides B (csrc/getrs.cu): the composed row permutation
+// and the transposed inverses of the diagonal blocks of L and U.
+template <typename T>
+struct SolvePlan {
+    int n = 0;
+    const T* LU = nullptr;
+    int lda = 0;
+    int* perm = nullptr;
+    T* DT = nullptr;
+    int* off = nullptr;        // work items before each block step
+};
+template <typename T>
+int solve_plan_make(int n, const T* LU, int lda, const int* piv, SolvePlan<T>* p, cudaStream_t s);
+template <typename T>
+int solve_plan_apply(const SolvePlan<T>& p, int nrhs, T* B, int ldb, cudaStream_t s);
+template <typename T>
+void solve_plan_free(SolvePlan<T>* p, cudaStream_t s);
 int getrs_f32(int n, int nrhs, const float* LU, int lda, const int* piv, float* B, int ldb, cudaStream_t s);
 
 // Factorization + refinement pieces of the solver (csrc/ir.cu), shared with
@@ -105,6 +123,7 @@ struct IrFactors {
     int* piv = nullptr;
     int* info = nullptr;
     int precision = 0;         // LU_PREC_* of the factors
+    SolvePlan<float> plan;     // solve plan of these factors
 };
 int ir_factor(int n, const double* A, int lda, int prec, int b, int h, IrFactors* f, cudaStream_t s);
 int ir_refine(IrFactors* f, const double* A, int lda, int nrhs, const double* B, int ldb, double* X, int ldx,

@@ -2,13 +2,30 @@
 // The linear solve is what the paper's factorization serves ("linear
 // solvers", Section 1); the paper does not spell it out.
 //
-// 1. The swap sequence piv is composed into one permutation (one thread,
-//    in shared memory when it fits) and B is gathered into a workspace Y.
-// 2. Forward substitution with unit L, then back substitution with U, both
-//    blocked by NB rows with inverted diagonal blocks (below).
-// 3. The result is copied back into B.
+// A solve plan holds what depends on the factors only: the row permutation
+// composed from the swap sequence piv, and the inverses of the NB x NB
+// diagonal blocks of L (unit lower) and U (upper), stored transposed.  The
+// refinement keeps one plan per factorization; the one-shot entry points
+// build and drop one per call.
+//
+// Applying a plan: B is gathered through the permutation into Y (row stride
+// nc, padded to a width of 8, 16, 32 or 64), then one kernel runs the
+// blocked forward and backward substitutions as a list of work items taken
+// in order from an atomic counter.  Every item is a 32-row contraction:
+//   forward step b:   parts of X_b = inv(L_bb) Y_b (32 rows each), then for
+//                     every 32-row tile t below the block: Y_t -= L_tb X_b;
+//   backward step b:  (b from the last block up) the parts of
+//                     X_b = inv(U_bb) X_b, then the tiles above:
+//                     X_t -= U_tb X_b.
+// An item first stages its coefficient rows, then waits (bounded, through
+// per-tile and per-block counters) on items earlier in the list, which CTAs
+// already running have taken, so the kernel progresses whatever number of
+// its CTAs is resident.  Each tile takes its updates one step at a time, in
+// step order, so results do not depend on timing.  Right-hand sides go
+// through in passes of up to 64.
 #include "common.cuh"
 #include "prof.cuh"
+#include <mutex>
 
 namespace lu {
 
@@ -41,32 +58,8 @@ __global__ void perm_from_piv_global(int n, const int* __restrict__ piv, int* __
         }
 }
 
-template <typename T>
-__global__ void gather_rows(int n, int nrhs, const int* __restrict__ perm, const T* __restrict__ B, int ldb,
-                            T* __restrict__ Y) {
-    const long long tot = static_cast<long long>(n) * nrhs;
-    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < tot;
-         e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int i = static_cast<int>(e / nrhs), c = static_cast<int>(e % nrhs);
-        Y[e] = B[idx(perm[i], c, ldb)];
-    }
-}
-
-template <typename T>
-__global__ void copy_out(int n, int nrhs, const T* __restrict__ Y, T* __restrict__ B, int ldb) {
-    const long long tot = static_cast<long long>(n) * nrhs;
-    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < tot;
-         e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int i = static_cast<int>(e / nrhs), c = static_cast<int>(e % nrhs);
-        B[idx(i, c, ldb)] = Y[e];
-    }
-}
-
-// Blocked solves use the inverses of the diagonal blocks: one launch inverts
-// every NB x NB diagonal block of L (unit lower) and U (upper); each block
-// step is then  X_I = inv(D_I) Y_I  (a small product, several CTAs)  and
-// Y_J -= T_{J,I} X_I  for the rows that remain (grid-wide).  NB = 128 for
-// binary32, 64 for binary64 (two NB x NB tiles fit in shared memory).
+// Block size of the substitution: NB = 128 for binary32, 64 for binary64
+// (the inversion kernel holds two NB x NB tiles in shared memory).
 template <typename T>
 struct SolveNB {
     static constexpr int value = sizeof(T) == 4 ? 128 : 64;
@@ -112,94 +105,262 @@ __global__ void __launch_bounds__(128) invert_diag_kernel(int n, const T* __rest
         }
     }
     __syncthreads();
+    // transposed: out[p][i] = inv[i][p], so that a warp reads consecutive i
     T* out = Dinv + (static_cast<size_t>(blk) * 2 + kind) * NB * NB;
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) out[e] = Xs[(e / NB) * (NB + 1) + (e % NB)];
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) out[e] = Xs[(e % NB) * (NB + 1) + (e / NB)];
 }
 
-// X[r0+i][:] = sum_p D[i][p] Y[r0+p][:] for the rows this CTA owns (16 per CTA).
-template <typename T>
-__global__ void __launch_bounds__(256) diag_apply_kernel(int nrhs, int r0, int nb, const T* __restrict__ D,
-                                                         const T* __restrict__ Y, T* __restrict__ X) {
-    constexpr int NB = SolveNB<T>::value;
-    const int i0 = blockIdx.x * 16;
-    const int tot = 16 * nrhs;
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-        const int i = i0 + e / nrhs, c = e % nrhs;
-        if (i >= nb) continue;
-        T s = 0;
-        for (int p = 0; p < nb; ++p) s = fma(D[i * NB + p], Y[idx(r0 + p, c, nrhs)], s);
-        X[idx(r0 + i, c, nrhs)] = s;
+constexpr int kSolveRhs = 64;            // right-hand sides per pass
+constexpr int kSolveTile = 32;           // rows per update tile
+constexpr int kSolveThreads = 256;
+constexpr long long kSolveWaitLimit = 1ll << 24;   // polls of one dependency before giving up
+
+// Item list bookkeeping (device memory, zeroed before each pass).
+struct SolveSync {
+    int next;          // next item to take
+    int timeout;
+    int pad[2];
+};
+
+// Items before forward step b / backward step b: off[0..2*nblk], built once
+// per plan (the block size arrives in off[0]).
+__global__ void solve_offsets_kernel(int n, int* __restrict__ off) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    constexpr int TR = kSolveTile;
+    const int ntile = cdiv(n, TR);
+    const int NB = off[0];
+    const int nblk = cdiv(n, NB);
+    const int tpb = NB / TR;
+    int acc = 0;
+    for (int b = 0; b < nblk; ++b) {                    // forward
+        off[b] = acc;
+        const int parts = cdiv(min(NB, n - b * NB), TR);
+        acc += parts + ntile - min(ntile, (b + 1) * tpb);
+    }
+    for (int st = 0; st < nblk; ++st) {                 // backward, last block first
+        const int b = nblk - 1 - st;
+        off[nblk + st] = acc;
+        const int parts = cdiv(min(NB, n - b * NB), TR);
+        acc += parts + b * tpb;
+    }
+    off[2 * nblk] = acc;
+}
+
+// Bounded wait by thread 0 until *flag >= want; records a timeout.  After
+// any timeout every wait returns at once, so a broken run ends quickly.
+__device__ __forceinline__ void solve_wait(const int* flag, int want, SolveSync* sy) {
+    const volatile int* f = flag;
+    const volatile int* to = &sy->timeout;
+    long long it = 0;
+    while (*f < want) {
+        if (++it > kSolveWaitLimit || ((it & 255) == 0 && *to)) {
+            atomicExch(&sy->timeout, 1);
+            return;
+        }
+        __nanosleep(32);
     }
 }
 
-// Y[r][:] -= LU[r][r0:r0+nb] * X[r0:r0+nb][:] for r in [ra, rb).
-// nrhs >= 8: one thread per (row, column); else one warp per row.
-template <typename T>
-__global__ void __launch_bounds__(256) block_update(int nrhs, int ra, int rb, int r0, int nb,
-                                                    const T* __restrict__ LU, int lda, const T* __restrict__ X,
-                                                    T* __restrict__ Y) {
+// Forward (L: Y -> X) then backward (U: X -> Y) substitution; right-hand
+// sides row-major with stride NCW (columns >= nc are zero and stay zero).
+template <typename T, int NCW>
+__global__ void __launch_bounds__(kSolveThreads) solve_items_kernel(int n, const T* __restrict__ LU, int lda,
+                                                                    const T* __restrict__ DT,
+                                                                    const int* __restrict__ off, T* Y, T* X,
+                                                                    int* fdone, int* bdone, int* xpf, int* xpb,
+                                                                    SolveSync* sy) {
     constexpr int NB = SolveNB<T>::value;
+    constexpr int TR = kSolveTile;
+    constexpr int TPB = NB / TR;                     // tiles (and solve parts) per block
+    constexpr int MU = NCW / 8;                      // columns per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* Xs = reinterpret_cast<T*>(smem_raw);          // nb x nrhs
-    for (int e = threadIdx.x; e < nb * nrhs; e += blockDim.x) Xs[e] = X[static_cast<size_t>(r0) * nrhs + e];
-    __syncthreads();
-    if (nrhs >= 8) {
-        const long long pairs = static_cast<long long>(rb - ra) * nrhs;
-        for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < pairs;
-             e += static_cast<long long>(gridDim.x) * blockDim.x) {
-            const int r = ra + static_cast<int>(e / nrhs), c = static_cast<int>(e % nrhs);
-            const T* lrow = LU + idx(r, r0, lda);
-            T s = 0;
-            for (int p = 0; p < nb; ++p) s = fma(lrow[p], Xs[p * nrhs + c], s);
-            Y[idx(r, c, nrhs)] -= s;
-        }
-        return;
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int r = ra + blockIdx.x * nwarp + warp; r < rb; r += gridDim.x * nwarp) {
-        const T* lrow = LU + idx(r, r0, lda);
-        T lv[NB / 32];
-#pragma unroll
-        for (int e = 0; e < NB / 32; ++e) {
-            const int p = lane + 32 * e;
-            lv[e] = p < nb ? lrow[p] : T(0);
-        }
-        for (int c = 0; c < nrhs; ++c) {
-            T s = 0;
-#pragma unroll
-            for (int e = 0; e < NB / 32; ++e) {
-                const int p = lane + 32 * e;
-                if (p < nb) s = fma(lv[e], Xs[p * nrhs + c], s);
+    T* Ls = reinterpret_cast<T*>(smem_raw);          // TR x (NB+1): the item's coefficient rows
+    T* Bs = Ls + TR * (NB + 1);                      // NB x NCW: the right operand
+    __shared__ int s_item, s_ph, s_b, s_t, s_q;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = kSolveThreads / 32;
+    const int nblk = cdiv(n, NB), ntile = cdiv(n, TR);
+    const int total = off[2 * nblk];
+    int bs_key = -1;                                 // which block Bs holds: (ph * 2 + kind) * nblk + b
+    for (;;) {
+        if (tid == 0) {
+            const int item = atomicAdd(&sy->next, 1);
+            int ph = 0, b = 0, t = -1, q = 0;
+            if (item < total) {
+                int lo = 0, hi = 2 * nblk - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (off[mid] <= item) lo = mid; else hi = mid - 1;
+                }
+                const int k = item - off[lo];
+                ph = lo < nblk ? 0 : 1;
+                b = ph == 0 ? lo : nblk - 1 - (lo - nblk);
+                const int parts = cdiv(min(NB, n - b * NB), TR);
+                if (k < parts) q = k;
+                else t = ph == 0 ? (b + 1) * TPB + (k - parts) : b * TPB - 1 - (k - parts);
             }
+            s_item = item;
+            s_ph = ph;
+            s_b = b;
+            s_t = t;
+            s_q = q;
+        }
+        __syncthreads();
+        if (s_item >= total) break;
+        const int ph = s_ph, b = s_b, t = s_t, q = s_q;
+        const int r0 = b * NB, nb = min(NB, n - r0), parts = cdiv(nb, TR);
+        const bool part = t < 0;
+        // 1. the coefficient rows (independent of everything in flight)
+        const int ra = part ? r0 + q * TR : t * TR;      // first output row
+        const int nr = min(TR, (part ? r0 + nb : n) - ra);
+        if (part) {
+            const T* D = DT + (static_cast<size_t>(b) * 2 + ph) * NB * NB;   // D[p][i] = inv[i][p]
+            for (int p = warp; p < nb; p += nwarp)
+                if (lane < nr) Ls[lane * (NB + 1) + p] = D[static_cast<size_t>(p) * NB + q * TR + lane];
+        } else {
+            for (int i = warp; i < nr; i += nwarp)
+                for (int p = lane; p < nb; p += 32) Ls[i * (NB + 1) + p] = LU[idx(ra + i, r0 + p, lda)];
+        }
+        // 2. dependencies, all on earlier items
+        if (tid == 0) {
+            if (part) {
+                const int kb = ph == 0 ? b : nblk - 1 - b;
+                for (int u = b * TPB; u < min(ntile, (b + 1) * TPB); ++u)
+                    solve_wait(ph == 0 ? fdone + u : bdone + u, kb, sy);
+                if (ph == 1) solve_wait(xpf + b, parts, sy);
+            } else {
+                solve_wait(ph == 0 ? xpf + b : xpb + b, parts, sy);
+                if (ph == 1) {
+                    const int tb = t / TPB;
+                    solve_wait(xpf + tb, cdiv(min(NB, n - tb * NB), TR), sy);
+                }
+                solve_wait(ph == 0 ? fdone + t : bdone + t, ph == 0 ? b : nblk - 1 - b, sy);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        // 3. the right operand: the block's right-hand side (part) or its solution (tile);
+        //    written by other CTAs, so read past L1
+        const int key = (ph * 2 + (part ? 0 : 1)) * nblk + b;
+        if (bs_key != key) {
+            const T* src = part ? (ph == 0 ? Y : X) : (ph == 0 ? X : Y);
+            for (int e = tid; e < nb * NCW; e += kSolveThreads) Bs[e] = __ldcg(src + static_cast<size_t>(r0) * NCW + e);
+            bs_key = key;
+        }
+        __syncthreads();
+        // 4. 32 rows x NCW: out = Ls Bs
+        const int i = tid >> 3, cg = tid & 7;
+        T acc[MU];
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-            if (lane == 0) Y[idx(r, c, nrhs)] -= s;
+        for (int k = 0; k < MU; ++k) acc[k] = T(0);
+        if (i < nr) {
+#pragma unroll 4
+            for (int p = 0; p < nb; ++p) {
+                const T l = Ls[i * (NB + 1) + p];
+#pragma unroll
+                for (int k = 0; k < MU; ++k) acc[k] = fma(l, Bs[p * NCW + cg + 8 * k], acc[k]);
+            }
+            if (part) {
+                T* row = (ph == 0 ? X : Y) + static_cast<size_t>(ra + i) * NCW;
+#pragma unroll
+                for (int k = 0; k < MU; ++k) row[cg + 8 * k] = acc[k];
+            } else {
+                T* row = (ph == 0 ? Y : X) + static_cast<size_t>(ra + i) * NCW;
+#pragma unroll
+                for (int k = 0; k < MU; ++k) row[cg + 8 * k] = __ldcg(row + cg + 8 * k) - acc[k];
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            if (part) atomicAdd(ph == 0 ? xpf + b : xpb + b, 1);
+            else atomicAdd(ph == 0 ? fdone + t : bdone + t, 1);
         }
     }
 }
 
-template <typename T>
-int getrs_impl(int n, int nrhs, const T* LU, int lda, const int* piv, T* B, int ldb, int* perm, T* Y, T* X,
-               T* Dinv, cudaStream_t s) {
+template <typename T, int NCW>
+static size_t solve_smem() {
     constexpr int NB = SolveNB<T>::value;
+    return (static_cast<size_t>(kSolveTile) * (NB + 1) + static_cast<size_t>(NB) * NCW) * sizeof(T);
+}
+
+// CTAs of the item kernel: as many as fit on the device, up to 4 per SM
+// (none need to be resident together).
+template <typename T, int NCW>
+static int solve_grid() {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = solve_smem<T, NCW>();
+    if (smem_attr(solve_items_kernel<T, NCW>, smem) != 0) return -1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_items_kernel<T, NCW>, kSolveThreads, smem);
+    cudaGetLastError();
+    if (per < 1 || sms < 1) return -1;
+    return sms * (per < 4 ? per : 4);
+}
+
+template <typename T, int NCW>
+static int solve_launch(int n, const SolvePlan<T>& p, T* Y, T* X, int* fdone, int* bdone, int* xpf, int* xpb,
+                        SolveSync* sy, cudaStream_t s) {
+    const int G = solve_grid<T, NCW>();
+    if (G <= 0) return LU_EUNSUPPORTED;
+    solve_items_kernel<T, NCW><<<G, kSolveThreads, solve_smem<T, NCW>(), s>>>(n, p.LU, p.lda, p.DT, p.off, Y, X,
+                                                                              fdone, bdone, xpf, xpb, sy);
+    count_launches(1);
+    return 0;
+}
+
+// gather with zero padding: Y[i][c] = B[perm[i]][c0 + c] for c < nc, 0 for nc <= c < w
+template <typename T>
+__global__ void gather_rows_pad(int n, int nc, int w, const int* __restrict__ perm, const T* __restrict__ B, int ldb,
+                                T* __restrict__ Y) {
+    const long long tot = static_cast<long long>(n) * w;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < tot;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(e / w), c = static_cast<int>(e % w);
+        Y[e] = c < nc ? B[idx(perm[i], c, ldb)] : T(0);
+    }
+}
+
+template <typename T>
+__global__ void copy_out_pad(int n, int nc, int w, const T* __restrict__ Y, T* __restrict__ B, int ldb) {
+    const long long tot = static_cast<long long>(n) * nc;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < tot;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(e / nc), c = static_cast<int>(e % nc);
+        B[idx(i, c, ldb)] = Y[static_cast<size_t>(i) * w + c];
+    }
+}
+
+template <typename T>
+int solve_plan_make(int n, const T* LU, int lda, const int* piv, SolvePlan<T>* p, cudaStream_t s) {
+    constexpr int NB = SolveNB<T>::value;
+    *p = SolvePlan<T>{};
+    p->n = n;
+    p->LU = LU;
+    p->lda = lda;
+    if (n == 0) return 0;
+    const int nblk = cdiv(n, NB);
+    if (cudaMallocAsync(reinterpret_cast<void**>(&p->perm), sizeof(int) * static_cast<size_t>(n), s) != cudaSuccess ||
+        cudaMallocAsync(reinterpret_cast<void**>(&p->DT), sizeof(T) * static_cast<size_t>(nblk) * 2 * NB * NB, s) !=
+            cudaSuccess ||
+        cudaMallocAsync(reinterpret_cast<void**>(&p->off), sizeof(int) * (2 * static_cast<size_t>(nblk) + 1), s) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        solve_plan_free(p, s);
+        return LU_ENOMEM;
+    }
     if (n <= kPermSmemMax) {
         const size_t smem = static_cast<size_t>(n) * sizeof(int);
         if (int rc_ = smem_attr(perm_from_piv_smem, smem)) return rc_;
         ProfScope ps(LU_PROF_SOLVE, s);
-        perm_from_piv_smem<<<1, 256, smem, s>>>(n, piv, perm);
+        perm_from_piv_smem<<<1, 256, smem, s>>>(n, piv, p->perm);
         count_launches(1);
     } else {
         ProfScope ps(LU_PROF_SOLVE, s);
-        perm_from_piv_global<<<1, 256, 0, s>>>(n, piv, perm);
-        count_launches(1);
-    }
-    LU_LAUNCHED();
-    const long long tot = static_cast<long long>(n) * nrhs;
-    const int gblocks = static_cast<int>(tot / 256 + 1 < 4096 ? tot / 256 + 1 : 4096);
-    const int nblk = cdiv(n, NB);
-    {
-        ProfScope ps(LU_PROF_SOLVE, s);
-        gather_rows<T><<<gblocks, 256, 0, s>>>(n, nrhs, perm, B, ldb, Y);
+        perm_from_piv_global<<<1, 256, 0, s>>>(n, piv, p->perm);
         count_launches(1);
     }
     LU_LAUNCHED();
@@ -207,55 +368,15 @@ int getrs_impl(int n, int nrhs, const T* LU, int lda, const int* piv, T* B, int 
         const size_t ismem = 2 * static_cast<size_t>(NB) * (NB + 1) * sizeof(T);
         if (int rc_ = smem_attr(invert_diag_kernel<T>, ismem)) return rc_;
         ProfScope ps(LU_PROF_SOLVE, s);
-        invert_diag_kernel<T><<<dim3(nblk, 2), 128, ismem, s>>>(n, LU, lda, Dinv);
+        invert_diag_kernel<T><<<dim3(nblk, 2), 128, ismem, s>>>(n, LU, lda, p->DT);
         count_launches(1);
     }
     LU_LAUNCHED();
-    const size_t usmem = static_cast<size_t>(NB) * nrhs * sizeof(T);
-    if (int rc_ = smem_attr(block_update<T>, usmem)) return rc_;
-    auto update_grid = [&](int rows) {
-        const long long work = (nrhs >= 8) ? static_cast<long long>(rows) * nrhs : static_cast<long long>(rows) * 32;
-        const long long g = (work + 255) / 256;
-        return static_cast<int>(g < 2048 ? (g > 0 ? g : 1) : 2048);
-    };
-    // forward: Y (= P B) -> X = L^{-1} P B
-    for (int bi = 0; bi < nblk; ++bi) {
-        const int r0 = bi * NB, nb = min(NB, n - r0);
-        {
-            ProfScope ps(LU_PROF_SOLVE, s);
-            diag_apply_kernel<T><<<cdiv(nb, 16), 256, 0, s>>>(nrhs, r0, nb, Dinv + static_cast<size_t>(bi) * 2 * NB * NB,
-                                                              Y, X);
-            count_launches(1);
-        }
-        LU_LAUNCHED();
-        const int rows = n - (r0 + nb);
-        if (rows > 0) {
-            ProfScope ps(LU_PROF_SOLVE, s, 2.0 * rows * nb * nrhs);
-            block_update<T><<<update_grid(rows), 256, usmem, s>>>(nrhs, r0 + nb, n, r0, nb, LU, lda, X, Y);
-            count_launches(1);
-        }
-        LU_LAUNCHED();
-    }
-    // backward: the forward result X becomes the right-hand side; Y receives U^{-1} X
-    for (int bi = nblk - 1; bi >= 0; --bi) {
-        const int r0 = bi * NB, nb = min(NB, n - r0);
-        {
-            ProfScope ps(LU_PROF_SOLVE, s);
-            diag_apply_kernel<T><<<cdiv(nb, 16), 256, 0, s>>>(
-                nrhs, r0, nb, Dinv + (static_cast<size_t>(bi) * 2 + 1) * NB * NB, X, Y);
-            count_launches(1);
-        }
-        LU_LAUNCHED();
-        if (r0 > 0) {
-            ProfScope ps(LU_PROF_SOLVE, s, 2.0 * r0 * nb * nrhs);
-            block_update<T><<<update_grid(r0), 256, usmem, s>>>(nrhs, 0, r0, r0, nb, LU, lda, Y, X);
-            count_launches(1);
-        }
-        LU_LAUNCHED();
-    }
     {
+        const int nbv = NB;
+        LU_TRY(cudaMemcpyAsync(p->off, &nbv, sizeof(int), cudaMemcpyHostToDevice, s));
         ProfScope ps(LU_PROF_SOLVE, s);
-        copy_out<T><<<gblocks, 256, 0, s>>>(n, nrhs, Y, B, ldb);
+        solve_offsets_kernel<<<1, 32, 0, s>>>(n, p->off);
         count_launches(1);
     }
     LU_LAUNCHED();
@@ -263,25 +384,96 @@ int getrs_impl(int n, int nrhs, const T* LU, int lda, const int* piv, T* B, int 
 }
 
 template <typename T>
-int getrs_alloc(int n, int nrhs, const T* LU, int lda, const int* piv, T* B, int ldb, cudaStream_t s) {
-    if (n == 0 || nrhs == 0) return 0;
+void solve_plan_free(SolvePlan<T>* p, cudaStream_t s) {
+    if (p->perm) cudaFreeAsync(p->perm, s);
+    if (p->DT) cudaFreeAsync(p->DT, s);
+    if (p->off) cudaFreeAsync(p->off, s);
+    p->perm = nullptr;
+    p->DT = nullptr;
+    p->off = nullptr;
+}
+
+template <typename T>
+int solve_plan_apply(const SolvePlan<T>& p, int nrhs, T* B, int ldb, cudaStream_t s) {
     constexpr int NB = SolveNB<T>::value;
-    const size_t vs = static_cast<size_t>(n) * nrhs;
-    const size_t dsz = static_cast<size_t>(cdiv(n, NB)) * 2 * NB * NB;
+    const int n = p.n;
+    if (n == 0 || nrhs == 0) return 0;
+    const int nblk = cdiv(n, NB), ntile = cdiv(n, kSolveTile);
+    const size_t vs = static_cast<size_t>(n) * kSolveRhs;
+    const size_t flags = sizeof(SolveSync) + sizeof(int) * (2 * static_cast<size_t>(ntile) + 2 * nblk);
+    const size_t fbytes = (flags + 255) / 256 * 256;
     void* ws = nullptr;
-    const size_t bytes = sizeof(int) * static_cast<size_t>(n) + 64 + sizeof(T) * (2 * vs + dsz) + 64;
-    if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
+    if (cudaMallocAsync(&ws, fbytes + sizeof(T) * 2 * vs, s) != cudaSuccess) {
         cudaGetLastError();
         return LU_ENOMEM;
     }
-    int* perm = static_cast<int*>(ws);
-    T* Y = reinterpret_cast<T*>(reinterpret_cast<uintptr_t>(perm + n + 16) & ~uintptr_t(15));
+    SolveSync* sy = static_cast<SolveSync*>(ws);
+    int* fdone = reinterpret_cast<int*>(sy + 1);
+    int* bdone = fdone + ntile;
+    int* xpf = bdone + ntile;
+    int* xpb = xpf + nblk;
+    T* Y = reinterpret_cast<T*>(static_cast<unsigned char*>(ws) + fbytes);
     T* X = Y + vs;
-    T* Dinv = X + vs;
-    int rc = getrs_impl<T>(n, nrhs, LU, lda, piv, B, ldb, perm, Y, X, Dinv, s);
+    int rc = 0;
+    int timeout = 0;
+    for (int c0 = 0; c0 < nrhs && !rc; c0 += kSolveRhs) {
+        const int nc = (nrhs - c0) < kSolveRhs ? (nrhs - c0) : kSolveRhs;
+        const int w = nc <= 8 ? 8 : nc <= 16 ? 16 : nc <= 32 ? 32 : 64;
+        const long long tot = static_cast<long long>(n) * w;
+        const int gblocks = static_cast<int>(tot / 256 + 1 < 4096 ? tot / 256 + 1 : 4096);
+        if (cudaMemsetAsync(ws, 0, flags, s) != cudaSuccess) {
+            rc = LU_ELAUNCH;
+            break;
+        }
+        {
+            ProfScope ps(LU_PROF_SOLVE, s);
+            gather_rows_pad<T><<<gblocks, 256, 0, s>>>(n, nc, w, p.perm, B + c0, ldb, Y);
+            count_launches(1);
+        }
+        {
+            ProfScope ps(LU_PROF_SOLVE, s, 2.0 * static_cast<double>(n) * n * nc);
+            rc = w == 8    ? solve_launch<T, 8>(n, p, Y, X, fdone, bdone, xpf, xpb, sy, s)
+                 : w == 16 ? solve_launch<T, 16>(n, p, Y, X, fdone, bdone, xpf, xpb, sy, s)
+                 : w == 32 ? solve_launch<T, 32>(n, p, Y, X, fdone, bdone, xpf, xpb, sy, s)
+                           : solve_launch<T, 64>(n, p, Y, X, fdone, bdone, xpf, xpb, sy, s);
+        }
+        if (rc) break;
+        {
+            ProfScope ps(LU_PROF_SOLVE, s);
+            copy_out_pad<T><<<gblocks, 256, 0, s>>>(n, nc, w, Y, B + c0, ldb);
+            count_launches(1);
+        }
+        if (cudaPeekAtLastError() != cudaSuccess) {
+            cudaGetLastError();
+            rc = LU_ELAUNCH;
+            break;
+        }
+        int to = 0;
+        if (cudaMemcpyAsync(&to, &sy->timeout, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            rc = LU_ELAUNCH;
+            break;
+        }
+        timeout |= to;
+    }
+    if (!rc && timeout) rc = LU_ETIMEOUT;
     cudaFreeAsync(ws, s);
     return rc;
 }
+
+template <typename T>
+int getrs_alloc(int n, int nrhs, const T* LU, int lda, const int* piv, T* B, int ldb, cudaStream_t s) {
+    if (n == 0 || nrhs == 0) return 0;
+    SolvePlan<T> p;
+    int rc = solve_plan_make<T>(n, LU, lda, piv, &p, s);
+    if (!rc) rc = solve_plan_apply<T>(p, nrhs, B, ldb, s);
+    solve_plan_free<T>(&p, s);
+    return rc;
+}
+
+template int solve_plan_make<float>(int, const float*, int, const int*, SolvePlan<float>*, cudaStream_t);
+template int solve_plan_apply<float>(const SolvePlan<float>&, int, float*, int, cudaStream_t);
+template void solve_plan_free<float>(SolvePlan<float>*, cudaStream_t);
 
 int getrs_f64(int n, int nrhs, const double* LU, int lda, const int* piv, double* B, int ldb, cudaStream_t s) {
     return getrs_alloc<double>(n, nrhs, LU, lda, piv, B, ldb, s);

@@ -374,6 +374,7 @@ struct IrCtx {
     int ldx;
     float* A32;       // factors (fp32 storage)
     int* piv;
+    const SolvePlan<float>* plan;   // their solve plan
     double* R;        // n x nrhs
     float* r32;       // n x nrhs
     double* part;     // reduction partials
@@ -392,7 +393,7 @@ int precond_apply(IrCtx& c, const double* V, double* Z, double* scale) {
         count_launches(1);
     }
     LU_LAUNCHED();
-    if (int rc = getrs_f32(c.n, c.nrhs, c.A32, c.n, c.piv, c.r32, c.nrhs, c.s)) return rc;
+    if (int rc = solve_plan_apply<float>(*c.plan, c.nrhs, c.r32, c.nrhs, c.s)) return rc;
     {
         ProfScope ps(LU_PROF_OTHER, c.s);
         from_f32_scaled<<<grid_for(static_cast<long long>(c.n) * c.nrhs), 256, 0, c.s>>>(c.n, c.nrhs, c.r32, scale, Z,
@@ -564,10 +565,14 @@ int ir_factor(int n, const double* A, int lda, int prec, int b, int h, IrFactors
     fo.h = h;
     fo.precision = prec;
     f->precision = prec;
-    return lu_factor_f32(n, n, f->A32, n, f->piv, f->info, &fo, s);
+    if (int rc = lu_factor_f32(n, n, f->A32, n, f->piv, f->info, &fo, s)) return rc;
+    // the solve plan of the new factors (permutation, inverse diagonal blocks)
+    solve_plan_free<float>(&f->plan, s);
+    return solve_plan_make<float>(n, f->A32, n, f->piv, &f->plan, s);
 }
 
 void ir_release(IrFactors* f, cudaStream_t s) {
+    solve_plan_free<float>(&f->plan, s);
     if (f->A32) cudaFreeAsync(f->A32, s);
     if (f->piv) cudaFreeAsync(f->piv, s);
     if (f->info) cudaFreeAsync(f->info, s);
@@ -609,6 +614,7 @@ int ir_refine(IrFactors* fac, const double* A, int lda, int nrhs, const double* 
     c.s = stream;
     c.A32 = fac->A32;
     c.piv = fac->piv;
+    c.plan = &fac->plan;
     const size_t vs = static_cast<size_t>(n) * nrhs;
     c.R = dev.alloc<double>(vs);
     c.r32 = dev.alloc<float>(vs);
@@ -632,7 +638,7 @@ int ir_refine(IrFactors* fac, const double* A, int lda, int nrhs, const double* 
         count_launches(1);
     }
     LU_LAUNCHED();
-    if (int rc = getrs_f32(n, nrhs, c.A32, n, c.piv, c.r32, nrhs, stream)) return rc;
+    if (int rc = solve_plan_apply<float>(*c.plan, nrhs, c.r32, nrhs, stream)) return rc;
     {
         ProfScope ps(LU_PROF_OTHER, stream);
         from_f32_scaled<<<grid_for(static_cast<long long>(vs)), 256, 0, stream>>>(n, nrhs, c.r32, bmax, X, ldx, 0);
