@@ -12,7 +12,8 @@
 //   schur_tc_kernel      persistent tcgen05 GEMM, 128 x 128 tiles, K = 256
 // The GEMM's warps: warp 0 issues TMA loads, warp 1 owns tensor memory and
 // issues the MMAs (one elected thread), warps 2-5 run the epilogue
-// (tcgen05.ld -> fused C update in global memory).  Every mbarrier wait is
+// (tcgen05.ld -> fused C update in global memory; each thread loads its
+// row of the C tile before waiting for the accumulator).  Every mbarrier wait is
 // bounded; a wait that runs out sets an abort flag, the CTA drains and frees
 // its tensor memory, and the host sees info = -LU_ETIMEOUT.
 #include "common.cuh"
@@ -269,20 +270,42 @@ __global__ void __launch_bounds__(kTcThreads, 1) schur_tc_kernel(const __grid_co
         for (long long t = t0; t < t1; ++t) {
             const int it = static_cast<int>(t - t0), st = it & 1;
             const int mb = static_cast<int>(t / NB), nb = static_cast<int>(t % NB);
+            const int r = mb * kTcBM + q * 32 + lane;
+            float* crow = a.C + idx(r < a.M ? r : 0, nb * kTcBN, a.ldc);
+            // C does not depend on the accumulator: a full row segment is
+            // loaded before the wait, so the tile's 64 KB are in flight
+            // while the MMAs run.
+            const bool whole = a.vec4 && r < a.M && a.N - nb * kTcBN >= kTcBN;
+            float4 cpre[kTcBN / 4];
+            if (whole) {
+                const float4* p4 = reinterpret_cast<const float4*>(crow);
+#pragma unroll
+                for (int i = 0; i < kTcBN / 4; ++i) cpre[i] = p4[i];
+            }
             if (!mbar_wait(acc_full + st, (it >> 1) & 1, abort_flag)) break;
             tc_fence_after();
-            const int r = mb * kTcBM + q * 32 + lane;
             int e = 0;
             if (a.expL) e += a.expL[(a.row_base + mb * kTcBM) / kScaleTile];
             if (a.expU) e += a.expU[(a.col_base + nb * kTcBN) / kScaleTile];
             const float sc = ldexpf(1.0f, e);
-            float* crow = a.C + idx(r < a.M ? r : 0, nb * kTcBN, a.ldc);
+#pragma unroll
             for (int c = 0; c < kTcBN; c += 32) {
                 float v[32];
                 tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(st * kTcBN + c), v);
                 if (r < a.M) {
                     const int cmax = a.N - nb * kTcBN - c;       // valid columns in this chunk
-                    if (a.vec4 && cmax >= 32) {
+                    if (whole) {
+                        float4* p4 = reinterpret_cast<float4*>(crow + c);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            float4 x = cpre[c / 4 + i];
+                            x.x = fmaf(-sc, v[4 * i + 0], x.x);
+                            x.y = fmaf(-sc, v[4 * i + 1], x.y);
+                            x.z = fmaf(-sc, v[4 * i + 2], x.z);
+                            x.w = fmaf(-sc, v[4 * i + 3], x.w);
+                            p4[i] = x;
+                        }
+                    } else if (a.vec4 && cmax >= 32) {
                         float4* p4 = reinterpret_cast<float4*>(crow + c);
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
