@@ -72,12 +72,14 @@ static int factor_loop(int m, int n, T* A, int lda, int* piv, int* info, int b, 
     T* a00 = static_cast<T*>(ws.a00);
     int lo = 0, hi = 0;
     cudaStream_t s2 = nullptr;
-    cudaEvent_t ev_panel = nullptr, ev_tslu = nullptr;
+    cudaEvent_t ev_panel = nullptr, ev_tslu = nullptr, ev_piv = nullptr, ev_u12 = nullptr;
     int rc = 0;
     if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
         cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev_tslu, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&ev_tslu, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_piv, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_u12, cudaEventDisableTiming) != cudaSuccess)
         rc = LU_ELAUNCH;
     const int* root = nullptr;
     if (!rc && cudaEventRecord(ev_panel, s) != cudaSuccess) rc = LU_ELAUNCH;
@@ -91,8 +93,15 @@ static int factor_loop(int m, int n, T* A, int lda, int* piv, int* info, int b, 
         const int wn = (kmax - kn) < b ? (kmax - kn) : b;     // next panel width (<= 0: none)
         if (cudaStreamWaitEvent(s, ev_tslu, 0) != cudaSuccess) { rc = LU_ELAUNCH; break; }
         rc = pivot_apply<T>(A, lda, m, n, k, w, root, a00, piv, ws.mv, s);
+        // L21 (rows below the panel) and U12 (columns right of it) only read
+        // A00: U12 runs on the side stream beside L21, filling each other's
+        // last waves.
+        if (!rc && cudaEventRecord(ev_piv, s) != cudaSuccess) rc = LU_ELAUNCH;
+        if (!rc && cudaStreamWaitEvent(s2, ev_piv, 0) != cudaSuccess) rc = LU_ELAUNCH;
+        if (!rc) rc = trsm_u12<T>(A, lda, n, k, w, s2);
+        if (!rc && cudaEventRecord(ev_u12, s2) != cudaSuccess) rc = LU_ELAUNCH;
         if (!rc) rc = trsm_l21<T>(A, lda, m, k, w, s);
-        if (!rc) rc = trsm_u12<T>(A, lda, n, k, w, s);
+        if (!rc && cudaStreamWaitEvent(s, ev_u12, 0) != cudaSuccess) rc = LU_ELAUNCH;
         if (rc) break;
         if (wn > 0) {
             rc = schur(A, lda, m, k, w, kn, kn + wn, s);
@@ -114,6 +123,8 @@ static int factor_loop(int m, int n, T* A, int lda, int* piv, int* info, int b, 
     ws_free(ws, s);
     if (ev_panel) cudaEventDestroy(ev_panel);
     if (ev_tslu) cudaEventDestroy(ev_tslu);
+    if (ev_piv) cudaEventDestroy(ev_piv);
+    if (ev_u12) cudaEventDestroy(ev_u12);
     if (s2) cudaStreamDestroy(s2);
     return rc;
 }

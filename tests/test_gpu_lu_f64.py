@@ -156,7 +156,8 @@ def test_empty_matrix():
     assert int(info.cpu()[0]) == 0
 
 
-@pytest.mark.parametrize("n,nrhs", [(1, 1), (64, 1), (65, 3), (500, 8), (1030, 64)])
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (64, 1), (65, 3), (500, 8), (1030, 64), (300, 33), (257, 65),
+                                    (1030, 130), (200, 384)])
 def test_solve_multi_rhs(oracle_mod, n, nrhs):
     torch = cuda_or_fail()
     g = lib()

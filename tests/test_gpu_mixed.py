@@ -64,6 +64,31 @@ def test_f32_ties_and_zero_pivots(oracle_mod, n, b, h):
     np.testing.assert_array_equal(LUg, LUo)
 
 
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (129, 5), (1000, 16), (777, 40), (513, 100)])
+def test_f32_solve(oracle_mod, n, nrhs):
+    """Binary32 solve with binary32 factors: passes of up to 64 right-hand
+    sides at padded widths 8 / 16 / 32 / 64; compared with the oracle's
+    binary32 substitution within the rounding-error bound of both."""
+    torch = cuda_or_fail()
+    g, nat, L = native()
+    A = wl.matrix_uniform(n, n, seed=n + 3, stream=40).astype(np.float32)
+    B = wl.matrix_uniform(n, nrhs, seed=n + 3, stream=41).astype(np.float32)
+    LUo, po, io = oracle_mod.lu_factor_f32(A, b=32, h=64)
+    assert io == 0
+    dLU = torch.from_numpy(LUo).cuda()
+    dpiv = torch.from_numpy(po.astype(np.int32)).cuda()
+    dB = torch.from_numpy(B.copy()).cuda()
+    from paper_2010_05975_gb300 import api
+    api.lu_solve_f32(dLU, dpiv, dB)
+    torch.cuda.synchronize()
+    X = dB.cpu().numpy().astype(np.float64)
+    Xo = oracle_mod.lu_solve_f32(LUo, po, B).astype(np.float64)
+    cond = np.linalg.cond(A.astype(np.float64))
+    eps32 = np.finfo(np.float32).eps
+    assert np.abs(X - Xo).max() <= 64 * n * eps32 * cond * np.abs(Xo).max()
+    assert oracle_mod.backward_error(A.astype(np.float64), B.astype(np.float64), X).max() <= 20 * n * eps32
+
+
 def run_gemm_lowp(L32, U32, C32, fp8):
     torch = cuda_or_fail()
     g, nat, Lb = native()
