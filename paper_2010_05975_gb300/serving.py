@@ -102,6 +102,9 @@ class Server:
                     left.discard(t)
             if left:
                 if time.time() - t0 > timeout_s:
-                    raise TimeoutError(f"{len(left)} requests still pending")
+                    # say whether they sit in the queue or in a running solve
+                    states = {t: self.poll(t)["status"] for t in sorted(left)}
+                    raise TimeoutError(f"{len(left)} requests still pending after {timeout_s:.0f} s: "
+                                       f"{states}; server {self.stats()}")
                 time.sleep(sleep_s)
         return out

@@ -10,6 +10,8 @@ from tests.gpu_util import cuda_or_fail, lib
 
 pytestmark = pytest.mark.gpu
 
+WAIT_S = 240.0     # a request that takes longer than this is stuck, not slow
+
 
 def problems():
     rng_sizes = [32, 100, 257, 512, 1000, 64, 2048, 300, 777, 128]
@@ -30,14 +32,14 @@ def test_mix_equals_alone_and_reaches_tolerance(oracle_mod):
     budget = 24 << 30
     with g.Server(budget, max_slots=4) as srv:
         tickets = [srv.enqueue(A, B) for A, B, _, _ in probs]
-        mixed = srv.wait(tickets)
+        mixed = srv.wait(tickets, timeout_s=WAIT_S)
         st = srv.stats()
     assert st["peak_bytes"] <= budget and st["peak_running"] > 1
     alone = []
     with g.Server(budget, max_slots=1) as srv:
         for A, B, _, _ in probs:
             t = srv.enqueue(A, B)
-            alone.append(srv.wait([t])[t])
+            alone.append(srv.wait([t], timeout_s=WAIT_S)[t])
     for (A, B, Xt, kappa), t, ra in zip(probs, tickets, alone):
         rm = mixed[t]
         assert rm["status"] == "done" and ra["status"] == "done", (rm, ra)
@@ -55,9 +57,9 @@ def test_factor_cache_reuse(oracle_mod):
     B2 = wl.matrix_normal(700, 4, seed=7)
     with g.Server(8 << 30, max_slots=2) as srv:
         t1 = srv.enqueue(A, B1, matrix_id=42)
-        r1 = srv.wait([t1])[t1]
+        r1 = srv.wait([t1], timeout_s=WAIT_S)[t1]
         t2 = srv.enqueue(A, B2, matrix_id=42)
-        r2 = srv.wait([t2])[t2]
+        r2 = srv.wait([t2], timeout_s=WAIT_S)[t2]
     assert r1["cache_hit"] == 0 and r2["cache_hit"] == 1
     assert oracle_mod.backward_error(A, B2, r2["X"]).max() <= 1e-12
 
@@ -71,7 +73,7 @@ def test_singular_request_fails_alone():
     with g.Server(8 << 30, max_slots=2) as srv:
         tb = srv.enqueue(bad, np.ones((n, 1)))
         tg = [srv.enqueue(A, np.ones((n, 2))) for A in good]
-        res = srv.wait([tb] + tg)
+        res = srv.wait([tb] + tg, timeout_s=WAIT_S)
     assert res[tb]["status"] == "failed"
     assert all(res[t]["status"] == "done" and res[t]["eta"] <= 1e-12 for t in tg)
 
@@ -83,7 +85,7 @@ def test_device_inputs():
     B = wl.matrix_normal(256, 3, seed=10)
     with g.Server(4 << 30, max_slots=1) as srv:
         t = srv.enqueue(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())
-        r = srv.wait([t])[t]
+        r = srv.wait([t], timeout_s=WAIT_S)[t]
     assert r["status"] == "done" and r["eta"] <= 1e-12
 
 
@@ -98,6 +100,6 @@ def test_borrowed_inputs_match_copied():
         t1 = srv.enqueue(A, B)
         t2 = srv.enqueue(dA, dB, borrow=True)
         t3 = srv.enqueue(A, B, borrow=True)
-        res = srv.wait([t1, t2, t3])
+        res = srv.wait([t1, t2, t3], timeout_s=WAIT_S)
     np.testing.assert_array_equal(res[t1]["X"], res[t2]["X"])
     np.testing.assert_array_equal(res[t1]["X"], res[t3]["X"])
