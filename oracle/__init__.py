@@ -20,6 +20,10 @@ Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
   binary32; pinned by LAPACK sgetrf (b = 1) and exact dyadic L*U products.
 * ``round_lowp``     -- pinned against torch's bfloat16 / float8_e4m3fn
   conversions (round to nearest even) and hand-worked ties and saturation.
+* ``chol_factor`` / ``chol_solve`` (binary64 and binary32) -- pinned by exact
+  integer factors L (A = L L^T recovered bit for bit), numpy's Cholesky and
+  solve, the info of matrices with a known first non-positive pivot, the
+  untouched upper triangle, and the 1 x 1 and diagonal special cases.
 * ``e4m3_exponent``, ``gemm_lowp`` -- pinned by hand-worked exponents and by
   exactly representable operands, where the update equals the binary64
   product.
@@ -37,4 +41,6 @@ from .oracle import (  # noqa: F401
     round_lowp,
     e4m3_exponent,
     gemm_lowp,
+    chol_factor,
+    chol_solve,
 )

@@ -40,6 +40,11 @@
  *     (no division); in A00 and L21 such a column of L is set to zero and
  *     info records the first one (1-based), as LAPACK getrf does.
  *
+ * The same file holds the Cholesky factorization A = L L^T and its solve
+ * (the kernel Section 2.2 and the Conclusions name for the same schedule;
+ * no pivoting): right-looking, lower triangle only, one fused multiply-add
+ * per update term, then the column's square root or division.
+ *
  * Every update term is a = fma(-l, u, a) with the summation index ascending,
  * so any blocking that keeps that per-element order gives bit-identical
  * numbers.  Build with -ffp-contract=off so that no other expression fuses.
@@ -64,21 +69,25 @@ void oracle_gemm_lowp(int M, int N, int K, const float *L, int ldl, const float 
 #define REAL double
 #define FMA fma
 #define FABS fabs
+#define SQRT sqrt
 #define FN(name) name
 #include "lu_oracle_body.h"
 #undef REAL
 #undef FMA
 #undef FABS
+#undef SQRT
 #undef FN
 
 #define REAL float
 #define FMA fmaf
 #define FABS fabsf
+#define SQRT sqrtf
 #define FN(name) name##_f32
 #include "lu_oracle_body.h"
 #undef REAL
 #undef FMA
 #undef FABS
+#undef SQRT
 #undef FN
 
 /* ------------------------------------------------------------------------ */

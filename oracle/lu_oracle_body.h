@@ -328,3 +328,76 @@ int FN(oracle_lu_solve)(int n, int nrhs, const REAL *LU, int lda, const int *piv
     return 0;
 }
 
+
+/* ------------------------------------------------------------------------ */
+/* Cholesky factorization A = L L^T of a symmetric positive definite n x n   */
+/* matrix (Section 2.2 names Cholesky as a further kernel for the same       */
+/* schedule; the Conclusions name it as the next one).  Right-looking, one   */
+/* column at a time, reading and writing the lower triangle only:            */
+/*   l_jj = sqrt(a_jj);  l_ij = a_ij / l_jj (i > j);                          */
+/*   a_ic = fma(-l_ij, l_cj, a_ic) for j < c <= i,                             */
+/* so every element receives its update terms in ascending j before its     */
+/* own square root or division.  The first column whose a_jj is not > 0     */
+/* (or is NaN) stops the factorization with *info = j + 1 (LAPACK potrf's   */
+/* convention); columns before it hold L, the rest is as far as it got.     */
+/* The strict upper triangle is not referenced.                              */
+/* ------------------------------------------------------------------------ */
+int FN(oracle_chol_factor)(int n, REAL *A, int lda, int *info)
+{
+    if (n < 0) return -1;
+    if (lda < (n > 1 ? n : 1)) return -3;
+    *info = 0;
+    for (int j = 0; j < n; ++j) {
+        REAL d = IDX(A, lda, j, j);
+        if (!(d > (REAL)0)) {
+            *info = j + 1;
+            return 0;
+        }
+        REAL ljj = SQRT(d);
+        IDX(A, lda, j, j) = ljj;
+        for (int i = j + 1; i < n; ++i)
+            IDX(A, lda, i, j) = IDX(A, lda, i, j) / ljj;
+        for (int i = j + 1; i < n; ++i) {
+            REAL lij = IDX(A, lda, i, j);
+            for (int c = j + 1; c <= i; ++c)
+                IDX(A, lda, i, c) = FMA(-lij, IDX(A, lda, c, j), IDX(A, lda, i, c));
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Solve A X = B with the Cholesky factor L (lower triangle of L):           */
+/* L Y = B by forward substitution, then L^T X = Y by backward              */
+/* substitution; each element receives its terms in ascending (forward) or */
+/* descending (backward) index order and then one division by l_ii.         */
+/* B is n x nrhs row-major (ldb >= nrhs), overwritten with X.               */
+/* ------------------------------------------------------------------------ */
+int FN(oracle_chol_solve)(int n, int nrhs, const REAL *L, int lda, REAL *B, int ldb)
+{
+    if (n < 0) return -1;
+    if (nrhs < 0) return -2;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (ldb < (nrhs > 1 ? nrhs : 1)) return -6;
+    for (int i = 0; i < n; ++i) {
+        for (int p = 0; p < i; ++p) {
+            REAL l = IDX(L, lda, i, p);
+            for (int c = 0; c < nrhs; ++c)
+                IDX(B, ldb, i, c) = FMA(-l, IDX(B, ldb, p, c), IDX(B, ldb, i, c));
+        }
+        REAL d = IDX(L, lda, i, i);
+        for (int c = 0; c < nrhs; ++c)
+            IDX(B, ldb, i, c) = IDX(B, ldb, i, c) / d;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        for (int p = n - 1; p > i; --p) {
+            REAL l = IDX(L, lda, p, i);
+            for (int c = 0; c < nrhs; ++c)
+                IDX(B, ldb, i, c) = FMA(-l, IDX(B, ldb, p, c), IDX(B, ldb, i, c));
+        }
+        REAL d = IDX(L, lda, i, i);
+        for (int c = 0; c < nrhs; ++c)
+            IDX(B, ldb, i, c) = IDX(B, ldb, i, c) / d;
+    }
+    return 0;
+}

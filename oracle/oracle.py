@@ -70,6 +70,11 @@ def _load():
             lib.oracle_gemm_lowp.restype = None
             lib.oracle_round_array.argtypes = [P, P, ctypes.c_longlong, I]
             lib.oracle_round_array.restype = None
+            for suf in ("", "_f32"):
+                getattr(lib, "oracle_chol_factor" + suf).argtypes = [I, P, I, P]
+                getattr(lib, "oracle_chol_factor" + suf).restype = I
+                getattr(lib, "oracle_chol_solve" + suf).argtypes = [I, I, P, I, P, I]
+                getattr(lib, "oracle_chol_solve" + suf).restype = I
             lib.oracle_e4m3_exponent.argtypes = [ctypes.c_float]
             lib.oracle_e4m3_exponent.restype = I
             _lib = lib
@@ -205,3 +210,36 @@ def gemm_lowp(L: np.ndarray, U: np.ndarray, C: np.ndarray, fp8: bool):
     lib.oracle_gemm_lowp(M, N, K, _ptr(L), max(K, 1), _ptr(U), max(N, 1), _ptr(C), max(N, 1),
                          1 if fp8 else 0, _ptr(Cref), _ptr(Sabs))
     return Cref, Sabs
+
+
+def chol_factor(A: np.ndarray, dtype=np.float64):
+    """Cholesky A = L L^T (lower triangle read and written, strict upper
+    untouched).  Returns (F, info): F is a new array whose lower triangle is
+    L (columns before info - 1 when info > 0); dtype float64 or float32
+    selects the binary64 or binary32 instance."""
+    lib = _load()
+    F = np.ascontiguousarray(A, dtype=dtype).copy()
+    n = F.shape[0]
+    assert F.shape == (n, n)
+    info = ctypes.c_int(0)
+    fn = lib.oracle_chol_factor if F.dtype == np.float64 else lib.oracle_chol_factor_f32
+    rc = fn(n, _ptr(F), max(n, 1), ctypes.byref(info))
+    if rc != 0:
+        raise ValueError(f"oracle_chol_factor: argument {-rc} invalid")
+    return F, info.value
+
+
+def chol_solve(F: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """X = L^{-T} L^{-1} B with L the lower triangle of F; B is n or n x nrhs.
+    The precision is F's (float64 or float32)."""
+    lib = _load()
+    F = np.ascontiguousarray(F)
+    n = F.shape[0]
+    vec = B.ndim == 1
+    X = np.ascontiguousarray(B.reshape(n, -1), dtype=F.dtype).copy()
+    nrhs = X.shape[1]
+    fn = lib.oracle_chol_solve if F.dtype == np.float64 else lib.oracle_chol_solve_f32
+    rc = fn(n, nrhs, _ptr(F), max(n, 1), _ptr(X), max(nrhs, 1))
+    if rc != 0:
+        raise ValueError(f"oracle_chol_solve: argument {-rc} invalid")
+    return X[:, 0] if vec else X

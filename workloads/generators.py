@@ -10,6 +10,7 @@ Workloads:
   * uniform entries in [-1, 1)                    (N=512 single matrix, batches)
   * N(0, 1) entries via Box-Muller                (N=32768 single matrix)
   * A = H1 diag(s) H2 with Householder products   (mixed precision + refinement)
+  * symmetric, uniform entries + n on the diagonal (Cholesky)
   * log-uniform sizes, Poisson arrival times      (batches, serving)
 """
 from __future__ import annotations
@@ -87,6 +88,36 @@ def matrix_normal(m: int, n: int, seed: int, stream: int = 0,
                   out: np.ndarray | None = None, threads: int | None = None) -> np.ndarray:
     """m x n row-major matrix, entries iid N(0, 1)."""
     return _fill(m, n, normal, seed, stream, out, threads)
+
+
+def matrix_spd(n: int, seed: int, stream: int = 0, shift: float | None = None,
+               out: np.ndarray | None = None, threads: int | None = None) -> np.ndarray:
+    """n x n symmetric matrix: a_ij = a_ji = Uniform[-1, 1) drawn at counter
+    min(i,j) * n + max(i,j), plus shift on the diagonal (default n, which
+    makes it strictly diagonally dominant with a positive diagonal, hence
+    positive definite; a small shift gives an indefinite matrix)."""
+    A = np.empty((n, n), dtype=np.float64) if out is None else out
+    rows_per = max(1, (1 << 22) // max(n, 1))
+    chunks = [(r, min(n, r + rows_per)) for r in range(0, n, rows_per)]
+    cols = np.arange(n, dtype=np.uint64)
+
+    def work(c):
+        r0, r1 = c
+        i = np.arange(r0, r1, dtype=np.uint64)[:, None]
+        lo = np.minimum(i, cols[None, :])
+        hi = np.maximum(i, cols[None, :])
+        A[r0:r1, :] = uniform_pm1(seed, stream, (lo * np.uint64(n) + hi).ravel()).reshape(r1 - r0, n)
+
+    nt = threads or min(32, os.cpu_count() or 1)
+    if len(chunks) == 1 or nt == 1:
+        for c in chunks:
+            work(c)
+    else:
+        with ThreadPoolExecutor(nt) as ex:
+            list(ex.map(work, chunks))
+    d = np.arange(n)
+    A[d, d] += float(n) if shift is None else shift
+    return A
 
 
 def _reflectors(n: int, count: int, seed: int, stream: int) -> np.ndarray:
