@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--ref-sample-n", type=int, default=4096,
                     help="order of the matrix the CPU oracle factors in each --impl reference step")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=["lu64", "mixed", "batched", "serving"], default="lu64",
+    ap.add_argument("--workload", choices=["lu64", "mixed", "batched", "serving", "cholesky"], default="lu64",
                     help="lu64: the FP64 factorization (default line); mixed: only the mixed-precision "
                          "refinement measurement")
     ap.add_argument("--mixed-n", type=int, default=32768)
@@ -309,6 +309,55 @@ def run_batched(a, dev, count=8192, warmup=2, steps=3):
 
 
 # ---------------------------------------------------------------------------
+# Cholesky: A = L L^T, N = 32768, symmetric Uniform[-1,1) + N I, b = 128
+# ---------------------------------------------------------------------------
+def run_cholesky(a, dev, n=32768, b=128, warmup=1, steps=2):
+    import torch
+    import paper_2010_05975_gb300 as g
+    import workloads as wl
+    flops = n ** 3 / 3.0
+    out = {"n": n, "b": b, "flops": "n^3/3", "input": f"symmetric Uniform[-1,1) + n I, seed {a.seed}",
+           "steps": steps, "warmup": warmup, "cases": []}
+    A = wl.matrix_spd(n, seed=a.seed)
+    stream = torch.cuda.current_stream(dev)
+    for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        pristine = torch.from_numpy(A).to(dev).to(dt)
+        work = torch.empty_like(pristine)
+        info = torch.empty(1, dtype=torch.int32, device=dev)
+        times = []
+        for it in range(warmup + steps + 1):
+            work.copy_(pristine)
+            torch.cuda.synchronize(dev)
+            prof = it == warmup + steps          # one more, profiled step (per-kernel event times)
+            if prof:
+                g.prof_begin()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.chol_factor(work, b=b, info=info, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if prof:
+                shares = g.prof_end()
+            elif it >= warmup:
+                times.append(e0.elapsed_time(e1) / 1e3)
+        t = float(np.median(times))
+        case = {"dtype": name, "factor_s": t, "tflops": flops / t / 1e12, "info": int(info.cpu()[0]),
+                "kernel_time_ms": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}
+                                   for k, v in shares.items()}}
+        sy = shares.get("syrk")
+        if sy and sy["ms"] > 0:
+            ach = sy["flops"] / (sy["ms"] / 1e3) / 1e12
+            case["syrk_tflops"] = ach
+            if name == "f64":
+                case["syrk_frac_of_fp64_peak"] = ach / FP64_PEAK_TFLOPS
+        out["cases"].append(case)
+        del pristine, work
+        torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # serving: Poisson arrivals, n log-uniform [32, 8192], 1-64 rhs,
 # kappa log-uniform [1e1, 1e6], 20% repeat matrix ids, 120 GB budget
 # ---------------------------------------------------------------------------
@@ -501,12 +550,14 @@ def run_ours(a):
     mixed = None
     batched = None
     serving = None
+    cholesky = None
     if not a.no_mixed and world == 1:
         del dA0, dA
         torch.cuda.empty_cache()
         mixed = run_mixed(a, dev, t_fp64_factor=tmax / a.steps)
         batched = run_batched(a, dev)
         serving = run_serving(a, dev)
+        cholesky = run_cholesky(a, dev)
 
     if rank != 0:
         if world > 1:
@@ -524,7 +575,7 @@ def run_ours(a):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": cfg, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
            "gpu_launches": launches, "kernel_time_ms": shares, "mixed_ir": mixed, "batched": batched,
-           "serving": serving}
+           "serving": serving, "cholesky": cholesky}
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -534,7 +585,7 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    elif a.workload in ("mixed", "batched", "serving"):
+    elif a.workload in ("mixed", "batched", "serving", "cholesky"):
         import torch
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
         torch.cuda.set_device(dev)
@@ -543,6 +594,9 @@ def main():
         if a.workload == "mixed":
             print(json.dumps({"metric": "IR solves/s at 1e-12 backward error", "unit": "solves/s",
                               "mixed_ir": run_mixed(a, dev)}), flush=True)
+        elif a.workload == "cholesky":
+            print(json.dumps({"metric": "Cholesky TFLOP/s (N^3/3)", "unit": "TFLOP/s",
+                              "cholesky": run_cholesky(a, dev)}), flush=True)
         elif a.workload == "batched":
             print(json.dumps({"metric": "batched LU matrices/s", "unit": "matrices/s",
                               "batched": run_batched(a, dev)}), flush=True)

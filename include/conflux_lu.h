@@ -1,5 +1,6 @@
 /*
- * conflux_lu.h -- C ABI of the GB300 tournament-pivoting LU library.
+ * conflux_lu.h -- C ABI of the GB300 tournament-pivoting LU library (and
+ * of its Cholesky variant).
  *
  * The operations follow the paper's statement of the problem: in-place
  * PA = LU of a dense matrix (Fig. 1; Algorithm 1, where A_t shrinks by v
@@ -129,6 +130,38 @@ int lu_factor_f32(int m, int n, float *A, int lda, int *piv, int *info,
 /* lu_solve_f32 -- X = U^{-1} L^{-1} P B with binary32 factors (B overwritten). */
 int lu_solve_f32(int n, int nrhs, const float *LU, int lda, const int *piv,
                  float *B, int ldb, cudaStream_t stream);
+
+/*
+ * chol_factor -- in-place Cholesky factorization A = L L^T of a symmetric
+ * positive definite n x n matrix, binary64 (the kernel that Section 2.2 and
+ * the Conclusions name for the same schedule; Algorithm 1's blocked
+ * right-looking loop without TournPivot: per step of width b, factor the
+ * diagonal block, solve the panel L21 = A21 L00^{-T}, update the lower
+ * triangle of the trailing matrix).
+ *   n      order, n >= 0
+ *   A      device, n x n row-major, lda >= max(1, n).  Only the lower
+ *          triangle (j <= i) is read; on return it holds L.  The strict
+ *          upper triangle is not referenced.
+ *   info   device int: 0, or j + 1 for the first column j whose pivot is not
+ *          positive (or is NaN).  The factorization is then incomplete:
+ *          columns before j hold L, later ones are unspecified (finite or
+ *          not; no device fault).
+ *   opts   may be NULL.  opts->b: panel width, 1..128 (default 128 for
+ *          n >= 4096, else 64); opts->h must be 0; opts->precision must be
+ *          0 or LU_PREC_F64.
+ * Every element receives its update terms in ascending column order as one
+ * fused multiply-add each, then its square root (diagonal) or one IEEE
+ * division, so the result does not depend on b.
+ * Returns 0, -i for an invalid argument i (1 n, 2 A, 3 lda, 4 info,
+ * 5 opts), or LU_ENOMEM / LU_ELAUNCH.
+ */
+int chol_factor(int n, double *A, int lda, int *info, const lu_opts *opts,
+                cudaStream_t stream);
+
+/* chol_factor_f32 -- the same factorization in binary32 (opts->precision 0
+ * or LU_PREC_F32). */
+int chol_factor_f32(int n, float *A, int lda, int *info, const lu_opts *opts,
+                    cudaStream_t stream);
 
 /*
  * lu_gemm_lowp -- the low-precision Schur update on its own:
@@ -341,7 +374,9 @@ int serve_destroy(serve_t *h);
 #define LU_PROF_SOLVE     6   /* getrs kernels                                   */
 #define LU_PROF_RESIDUAL  7   /* binary64 residual and backward error            */
 #define LU_PROF_OTHER     8   /* conversions, copies, scaling                    */
-#define LU_PROF_NCLASS    9
+#define LU_PROF_CHOL_DIAG 9   /* Cholesky diagonal-block factorization           */
+#define LU_PROF_SYRK      10  /* Cholesky trailing update (lower triangle)       */
+#define LU_PROF_NCLASS    11
 
 typedef struct {
     int kernel_class;        /* LU_PROF_*                                        */

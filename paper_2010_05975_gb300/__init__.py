@@ -30,6 +30,7 @@ from .api import (  # noqa: F401
     lu_factor_host,
     lu_factor_f32,
     lu_solve_f32,
+    chol_factor,
     lu_gemm_lowp,
     lu_residual,
     ir_solve,

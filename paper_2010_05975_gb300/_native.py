@@ -83,7 +83,8 @@ class lu_prof_entry(ctypes.Structure):
                 ("total_flops", ctypes.c_double), ("total_bytes", ctypes.c_double)]
 
 
-PROF_CLASSES = ["tslu", "pivot", "trsm_l21", "trsm_u12", "schur_f64", "schur_lowp", "solve", "residual", "other"]
+PROF_CLASSES = ["tslu", "pivot", "trsm_l21", "trsm_u12", "schur_f64", "schur_lowp", "solve", "residual", "other",
+                "chol_diag", "syrk"]
 
 _lock = threading.Lock()
 _lib = None
@@ -99,6 +100,8 @@ _SIGS = {
     "lu_factor_f32": ([I, I, P, I, P, P, ctypes.POINTER(lu_opts), P], I),
     "lu_solve_f32": ([I, I, P, I, P, P, I, P], I),
     "lu_gemm_lowp": ([I, I, I, P, I, P, I, P, I, I, P, P], I),
+    "chol_factor": ([I, P, I, P, ctypes.POINTER(lu_opts), P], I),
+    "chol_factor_f32": ([I, P, I, P, ctypes.POINTER(lu_opts), P], I),
     "lu_residual": ([I, I, P, I, P, I, P, I, P, I, P, P], I),
     "ir_solve": ([I, I, P, I, P, I, P, I, ctypes.POINTER(ir_opts), ctypes.POINTER(ir_result), P], I),
     "lu_factor_batched": ([I, P, P, P, P, P, I, P], I),

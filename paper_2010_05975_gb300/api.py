@@ -141,6 +141,28 @@ def lu_factor_f32(A: torch.Tensor, b: int = 0, h: int = 0, precision: int = nat.
     return piv[:k], info
 
 
+def chol_factor(A: torch.Tensor, b: int = 0, info: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """In-place Cholesky A = L L^T of a square float64 or float32 CUDA matrix
+    (lower triangle read and overwritten with L; strict upper untouched).
+    Returns info (int32 CUDA tensor, 0 or the first non-positive pivot's
+    column + 1); nothing is synchronised."""
+    if not isinstance(A, torch.Tensor) or A.dtype not in (torch.float64, torch.float32):
+        raise TypeError("A must be a float64 or float32 CUDA tensor")
+    _require(A, "A", A.dtype, 2)
+    n = A.shape[0]
+    if A.shape[1] != n:
+        raise ValueError("chol_factor needs a square matrix")
+    if info is None:
+        info = torch.empty(1, dtype=torch.int32, device=A.device)
+    opts = nat.lu_opts(b, 0, 0)
+    lib = nat.library()
+    fn, name = (lib.chol_factor, "chol_factor") if A.dtype == torch.float64 else \
+        (lib.chol_factor_f32, "chol_factor_f32")
+    rc = fn(n, A.data_ptr(), max(A.stride(0), 1), info.data_ptr(), ctypes.byref(opts), _stream_handle(stream))
+    nat.check(name, rc)
+    return info
+
+
 def lu_solve_f32(LU: torch.Tensor, piv: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
     _require(LU, "LU", torch.float32, 2)
     n = LU.shape[0]

@@ -100,7 +100,7 @@ static int factor_loop(int m, int n, T* A, int lda, int* piv, int* info, int b, 
         if (!rc && cudaStreamWaitEvent(s2, ev_piv, 0) != cudaSuccess) rc = LU_ELAUNCH;
         if (!rc) rc = trsm_u12<T>(A, lda, n, k, w, s2);
         if (!rc && cudaEventRecord(ev_u12, s2) != cudaSuccess) rc = LU_ELAUNCH;
-        if (!rc) rc = trsm_l21<T>(A, lda, m, k, w, s);
+        if (!rc) rc = trsm_l21<T>(A, lda, m, k, w, A + idx(k, k, lda), lda, s);
         if (!rc && cudaStreamWaitEvent(s, ev_u12, 0) != cudaSuccess) rc = LU_ELAUNCH;
         if (rc) break;
         if (wn > 0) {

@@ -87,13 +87,18 @@ int tslu_select(const T* A, int lda, int m, int k, int w, int h, int* lists, int
 template <typename T>
 int pivot_apply(T* A, int lda, int m, int n, int k, int w, const int* root_list, const T* a00, int* piv, int* mv,
                 cudaStream_t s);
+// L21 = A21 * U^{-1} with U the upper triangle of a w x w block (stride ldu)
 template <typename T>
-int trsm_l21(T* A, int lda, int m, int k, int w, cudaStream_t s);
+int trsm_l21(T* A, int lda, int m, int k, int w, const T* U, int ldu, cudaStream_t s);
 template <typename T>
 int trsm_u12(T* A, int lda, int n, int k, int w, cudaStream_t s);
 // A[r0:m, c0:c1) -= A[r0:m, k:k+w) * A[k:k+w, c0:c1)   (r0 = k + w)
 int schur_f64(double* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s);
 int schur_f32(float* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s);
+// Cholesky pieces (csrc/chol.cu, csrc/schur_f64.cu)
+constexpr int kCholMaxPanel = 128;      // largest Cholesky panel width
+template <typename T>
+int syrk_lower(T* A, int lda, int n, int k, int w, int c0, int c1, cudaStream_t s);
 int getrs_f64(int n, int nrhs, const double* LU, int lda, const int* piv, double* B, int ldb, cudaStream_t s);
 
 // What a solve needs besides B (csrc/getrs.cu): the composed row permutation

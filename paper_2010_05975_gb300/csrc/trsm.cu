@@ -1,5 +1,6 @@
 // FactorizeA10 and FactorizeA01 of Section 7.2 (binary64 or binary32):
-//   L21 = A21 * U00^{-1}   (rows below the panel, right solve, upper U00)
+//   L21 = A21 * U00^{-1}   (rows below the panel, right solve, upper U00;
+//                           with U00 = L00^T also the Cholesky panel solve)
 //   U12 = L00^{-1} * A12   (rows of the panel, left solve, unit lower L00)
 // Both keep a tile in shared memory and sweep the triangle right-looking,
 // so every element receives its fused updates in ascending pivot order and
@@ -16,8 +17,11 @@ constexpr int kU12Cols = 64;      // columns of A12 per CTA
 
 // Tile T[j][r] (column-major over the CTA's rows, padded stride).  Thread t
 // owns row r = t % 64 and columns c = j+1+g, j+1+g+4, ... with g = t / 64.
+// U (w x w, row stride ldu) is read on and above its diagonal only: the LU
+// passes A00 in place, the Cholesky factorization L00^T.
 template <typename E>
-__global__ void __launch_bounds__(256) trsm_l21_kernel(E* __restrict__ A, int lda, int m, int k, int w) {
+__global__ void __launch_bounds__(256) trsm_l21_kernel(E* __restrict__ A, int lda, int m, int k, int w,
+                                                       const E* __restrict__ U, int ldu) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     E* T = reinterpret_cast<E*>(smem_raw);
     const int r0 = k + w + blockIdx.x * kL21Rows;
@@ -30,7 +34,7 @@ __global__ void __launch_bounds__(256) trsm_l21_kernel(E* __restrict__ A, int ld
     __syncthreads();
     const int r = threadIdx.x % kL21Rows, g = threadIdx.x / kL21Rows;
     for (int j = 0; j < w; ++j) {
-        const E* Uj = A + idx(k + j, k, lda);
+        const E* Uj = U + idx(j, 0, ldu);
         if (g == 0) {
             const E u = Uj[j];
             const E a = T[j * kL21Stride + r];
@@ -67,14 +71,14 @@ __global__ void __launch_bounds__(256) trsm_u12_kernel(E* __restrict__ A, int ld
 }
 
 template <typename E>
-int trsm_l21(E* A, int lda, int m, int k, int w, cudaStream_t s) {
+int trsm_l21(E* A, int lda, int m, int k, int w, const E* U, int ldu, cudaStream_t s) {
     const int rows = m - k - w;
     if (rows <= 0) return 0;
     const size_t smem = static_cast<size_t>(w) * kL21Stride * sizeof(E);
     if (int rc_ = smem_attr(trsm_l21_kernel<E>, smem)) return rc_;
     {
         ProfScope ps(LU_PROF_TRSM_L21, s, static_cast<double>(rows) * w * w);
-        trsm_l21_kernel<E><<<cdiv(rows, kL21Rows), 256, smem, s>>>(A, lda, m, k, w);
+        trsm_l21_kernel<E><<<cdiv(rows, kL21Rows), 256, smem, s>>>(A, lda, m, k, w, U, ldu);
         count_launches(1);
     }
     LU_LAUNCHED();
@@ -96,8 +100,8 @@ int trsm_u12(E* A, int lda, int n, int k, int w, cudaStream_t s) {
     return 0;
 }
 
-template int trsm_l21<double>(double*, int, int, int, int, cudaStream_t);
-template int trsm_l21<float>(float*, int, int, int, int, cudaStream_t);
+template int trsm_l21<double>(double*, int, int, int, int, const double*, int, cudaStream_t);
+template int trsm_l21<float>(float*, int, int, int, int, const float*, int, cudaStream_t);
 template int trsm_u12<double>(double*, int, int, int, int, cudaStream_t);
 template int trsm_u12<float>(float*, int, int, int, int, cudaStream_t);
 

@@ -63,3 +63,21 @@ def test_python_layer_refuses_cpu_tensors(native):
     import torch
     with pytest.raises(TypeError):
         native.lu_factor(torch.zeros(4, 4, dtype=torch.float64))
+
+
+def test_chol_argument_errors_before_device_work(native):
+    lib = native.library()
+    s = ctypes.c_void_p(0)
+    dummy = ctypes.c_void_p(16)
+    nat = native._native
+    for fn in (lib.chol_factor, lib.chol_factor_f32):
+        assert fn(-1, dummy, 1, dummy, None, s) == -1
+        assert fn(4, None, 4, dummy, None, s) == -2
+        assert fn(4, dummy, 3, dummy, None, s) == -3
+        assert fn(4, dummy, 4, None, None, s) == -4
+        assert fn(4, dummy, 4, dummy, ctypes.byref(nat.lu_opts(129, 0, 0)), s) == -5   # b > 128
+        assert fn(4, dummy, 4, dummy, ctypes.byref(nat.lu_opts(64, 128, 0)), s) == -5  # h must be 0
+        assert fn(4, dummy, 4, dummy, ctypes.byref(nat.lu_opts(-1, 0, 0)), s) == -5
+    bad = nat.lu_opts(64, 0, nat.LU_PREC_BF16)
+    assert lib.chol_factor(4, dummy, 4, dummy, ctypes.byref(bad), s) == -5
+    assert lib.chol_factor_f32(4, dummy, 4, dummy, ctypes.byref(bad), s) == -5
