@@ -164,6 +164,22 @@ int chol_factor_f32(int n, float *A, int lda, int *info, const lu_opts *opts,
                     cudaStream_t stream);
 
 /*
+ * chol_solve -- X = L^{-T} L^{-1} B with the factor of chol_factor.
+ *   n, L, lda  as returned by chol_factor (device; lower triangle read)
+ *   nrhs  number of right-hand sides, 0 <= nrhs <= 384
+ *   B     device, n x nrhs row-major, ldb >= max(1, nrhs); overwritten by X
+ * Blocked forward and backward substitution (the LU solve's work list with
+ * U = L^T and no permutation).  Returns 0, -i for an invalid argument i
+ * (1 n, 2 nrhs, 3 L, 4 lda, 5 B, 6 ldb), or LU_ENOMEM / LU_ELAUNCH /
+ * LU_ETIMEOUT (a bounded device wait ran out).
+ */
+int chol_solve(int n, int nrhs, const double *L, int lda, double *B, int ldb,
+               cudaStream_t stream);
+/* chol_solve_f32 -- the same with a binary32 factor. */
+int chol_solve_f32(int n, int nrhs, const float *L, int lda, float *B, int ldb,
+                   cudaStream_t stream);
+
+/*
  * lu_gemm_lowp -- the low-precision Schur update on its own:
  *   C -= sL * sU * round(L / sL) * round(U / sU)
  * L: M x K (ldl), U: K x N (ldu), C: M x N (ldc), all binary32 device

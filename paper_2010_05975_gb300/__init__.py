@@ -31,6 +31,7 @@ from .api import (  # noqa: F401
     lu_factor_f32,
     lu_solve_f32,
     chol_factor,
+    chol_solve,
     lu_gemm_lowp,
     lu_residual,
     ir_solve,

@@ -102,6 +102,8 @@ _SIGS = {
     "lu_gemm_lowp": ([I, I, I, P, I, P, I, P, I, I, P, P], I),
     "chol_factor": ([I, P, I, P, ctypes.POINTER(lu_opts), P], I),
     "chol_factor_f32": ([I, P, I, P, ctypes.POINTER(lu_opts), P], I),
+    "chol_solve": ([I, I, P, I, P, I, P], I),
+    "chol_solve_f32": ([I, I, P, I, P, I, P], I),
     "lu_residual": ([I, I, P, I, P, I, P, I, P, I, P, P], I),
     "ir_solve": ([I, I, P, I, P, I, P, I, ctypes.POINTER(ir_opts), ctypes.POINTER(ir_result), P], I),
     "lu_factor_batched": ([I, P, P, P, P, P, I, P], I),

@@ -163,6 +163,23 @@ def chol_factor(A: torch.Tensor, b: int = 0, info: torch.Tensor | None = None, s
     return info
 
 
+def chol_solve(L: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
+    """Overwrite B (n or n x nrhs, L's dtype, CUDA) with the solution of
+    L L^T X = B, L the lower triangle of chol_factor's result."""
+    if not isinstance(L, torch.Tensor) or L.dtype not in (torch.float64, torch.float32):
+        raise TypeError("L must be a float64 or float32 CUDA tensor")
+    _require(L, "L", L.dtype, 2)
+    n = L.shape[0]
+    Bm = B.view(n, 1) if B.dim() == 1 else B
+    _require(Bm, "B", L.dtype, 2)
+    lib = nat.library()
+    fn, name = (lib.chol_solve, "chol_solve") if L.dtype == torch.float64 else (lib.chol_solve_f32, "chol_solve_f32")
+    rc = fn(n, Bm.shape[1], L.data_ptr(), max(L.stride(0), 1), Bm.data_ptr(), max(Bm.stride(0), 1),
+            _stream_handle(stream))
+    nat.check(name, rc)
+    return B
+
+
 def lu_solve_f32(LU: torch.Tensor, piv: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
     _require(LU, "LU", torch.float32, 2)
     n = LU.shape[0]

@@ -111,6 +111,7 @@ struct SolvePlan {
     int* perm = nullptr;
     T* DT = nullptr;
     int* off = nullptr;        // work items before each block step
+    int chol = 0;              // LU is a Cholesky factor L: U = L^T, no permutation
 };
 template <typename T>
 int solve_plan_make(int n, const T* LU, int lda, const int* piv, SolvePlan<T>* p, cudaStream_t s);

@@ -1,6 +1,7 @@
 // Solve A X = B with the factors P A = L U (getrs): X = U^{-1} L^{-1} P B.
 // The linear solve is what the paper's factorization serves ("linear
-// solvers", Section 1); the paper does not spell it out.
+// solvers", Section 1); the paper does not spell it out.  A Cholesky factor
+// L goes through the same machinery with U = L^T and no permutation.
 //
 // A solve plan holds what depends on the factors only: the row permutation
 // composed from the swap sequence piv, and the inverses of the NB x NB
@@ -66,10 +67,13 @@ struct SolveNB {
 };
 
 // One CTA per (block, factor): Dinv[blk][kind] = inv(diag block).  Thread c
-// owns column c of the inverse; the block stays in shared memory.
+// owns column c of the inverse; the block stays in shared memory.  With
+// chol set the factors are L (non-unit lower, from a Cholesky factorization)
+// and L^T: both kinds compute inv(L_bb), kind 1 stores inv(L_bb^T) =
+// inv(L_bb)^T.
 template <typename T>
 __global__ void __launch_bounds__(128) invert_diag_kernel(int n, const T* __restrict__ LU, int lda,
-                                                          T* __restrict__ Dinv) {
+                                                          T* __restrict__ Dinv, int chol) {
     constexpr int NB = SolveNB<T>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);              // NB x (NB+1)
@@ -83,7 +87,18 @@ __global__ void __launch_bounds__(128) invert_diag_kernel(int n, const T* __rest
     __syncthreads();
     const int c = threadIdx.x;
     if (c < NB) {
-        if (kind == 0) {
+        if (chol) {
+            for (int i = 0; i < NB; ++i) {
+                T s = (i == c) ? T(1) : T(0);
+                if (i >= c && i < nb && c < nb) {
+                    for (int p = c; p < i; ++p) s = fma(-S[i * (NB + 1) + p], Xs[p * (NB + 1) + c], s);
+                    s = s / S[i * (NB + 1) + i];
+                } else {
+                    s = T(0);
+                }
+                Xs[i * (NB + 1) + c] = s;
+            }
+        } else if (kind == 0) {
             for (int i = 0; i < NB; ++i) {
                 T s = (i == c) ? T(1) : T(0);
                 if (i > c && i < nb) {
@@ -107,7 +122,12 @@ __global__ void __launch_bounds__(128) invert_diag_kernel(int n, const T* __rest
     __syncthreads();
     // transposed: out[p][i] = inv[i][p], so that a warp reads consecutive i
     T* out = Dinv + (static_cast<size_t>(blk) * 2 + kind) * NB * NB;
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) out[e] = Xs[(e % NB) * (NB + 1) + (e / NB)];
+    if (chol && kind == 1) {
+        // out[p][i] = inv(L^T)[i][p] = inv(L)[p][i]
+        for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) out[e] = Xs[(e / NB) * (NB + 1) + (e % NB)];
+    } else {
+        for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) out[e] = Xs[(e % NB) * (NB + 1) + (e / NB)];
+    }
 }
 
 constexpr int kSolveRhs = 64;            // right-hand sides per pass
@@ -163,12 +183,13 @@ __device__ __forceinline__ void solve_wait(const int* flag, int want, SolveSync*
 
 // Forward (L: Y -> X) then backward (U: X -> Y) substitution; right-hand
 // sides row-major with stride NCW (columns >= nc are zero and stay zero).
+// With chol set, U is L^T: the backward tiles read L transposed.
 template <typename T, int NCW>
 __global__ void __launch_bounds__(kSolveThreads) solve_items_kernel(int n, const T* __restrict__ LU, int lda,
                                                                     const T* __restrict__ DT,
                                                                     const int* __restrict__ off, T* Y, T* X,
                                                                     int* fdone, int* bdone, int* xpf, int* xpb,
-                                                                    SolveSync* sy) {
+                                                                    SolveSync* sy, int chol) {
     constexpr int NB = SolveNB<T>::value;
     constexpr int TR = kSolveTile;
     constexpr int TPB = NB / TR;                     // tiles (and solve parts) per block
@@ -216,6 +237,10 @@ __global__ void __launch_bounds__(kSolveThreads) solve_items_kernel(int n, const
             const T* D = DT + (static_cast<size_t>(b) * 2 + ph) * NB * NB;   // D[p][i] = inv[i][p]
             for (int p = warp; p < nb; p += nwarp)
                 if (lane < nr) Ls[lane * (NB + 1) + p] = D[static_cast<size_t>(p) * NB + q * TR + lane];
+        } else if (chol && ph == 1) {
+            // U[ra + i][r0 + p] = L[r0 + p][ra + i]: lanes along the L row
+            for (int p = warp; p < nb; p += nwarp)
+                if (lane < nr) Ls[lane * (NB + 1) + p] = LU[idx(r0 + p, ra + lane, lda)];
         } else {
             for (int i = warp; i < nr; i += nwarp)
                 for (int p = lane; p < nb; p += 32) Ls[i * (NB + 1) + p] = LU[idx(ra + i, r0 + p, lda)];
@@ -307,7 +332,7 @@ static int solve_launch(int n, const SolvePlan<T>& p, T* Y, T* X, int* fdone, in
     const int G = solve_grid<T, NCW>();
     if (G <= 0) return LU_EUNSUPPORTED;
     solve_items_kernel<T, NCW><<<G, kSolveThreads, solve_smem<T, NCW>(), s>>>(n, p.LU, p.lda, p.DT, p.off, Y, X,
-                                                                              fdone, bdone, xpf, xpb, sy);
+                                                                              fdone, bdone, xpf, xpb, sy, p.chol);
     count_launches(1);
     return 0;
 }
@@ -334,6 +359,12 @@ __global__ void copy_out_pad(int n, int nc, int w, const T* __restrict__ Y, T* _
     }
 }
 
+__global__ void perm_identity(int n, int* __restrict__ perm) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) perm[i] = i;
+}
+
+// piv == nullptr: LU holds a Cholesky factor L (lower triangle), solved as
+// L (L^T X) = B with no permutation.
 template <typename T>
 int solve_plan_make(int n, const T* LU, int lda, const int* piv, SolvePlan<T>* p, cudaStream_t s) {
     constexpr int NB = SolveNB<T>::value;
@@ -341,6 +372,7 @@ int solve_plan_make(int n, const T* LU, int lda, const int* piv, SolvePlan<T>* p
     p->n = n;
     p->LU = LU;
     p->lda = lda;
+    p->chol = piv == nullptr ? 1 : 0;
     if (n == 0) return 0;
     const int nblk = cdiv(n, NB);
     if (cudaMallocAsync(reinterpret_cast<void**>(&p->perm), sizeof(int) * static_cast<size_t>(n), s) != cudaSuccess ||
@@ -352,7 +384,11 @@ int solve_plan_make(int n, const T* LU, int lda, const int* piv, SolvePlan<T>* p
         solve_plan_free(p, s);
         return LU_ENOMEM;
     }
-    if (n <= kPermSmemMax) {
+    if (p->chol) {
+        ProfScope ps(LU_PROF_SOLVE, s);
+        perm_identity<<<cdiv(n, 256) < 1024 ? cdiv(n, 256) : 1024, 256, 0, s>>>(n, p->perm);
+        count_launches(1);
+    } else if (n <= kPermSmemMax) {
         const size_t smem = static_cast<size_t>(n) * sizeof(int);
         if (int rc_ = smem_attr(perm_from_piv_smem, smem)) return rc_;
         ProfScope ps(LU_PROF_SOLVE, s);
@@ -368,7 +404,7 @@ int solve_plan_make(int n, const T* LU, int lda, const int* piv, SolvePlan<T>* p
         const size_t ismem = 2 * static_cast<size_t>(NB) * (NB + 1) * sizeof(T);
         if (int rc_ = smem_attr(invert_diag_kernel<T>, ismem)) return rc_;
         ProfScope ps(LU_PROF_SOLVE, s);
-        invert_diag_kernel<T><<<dim3(nblk, 2), 128, ismem, s>>>(n, LU, lda, p->DT);
+        invert_diag_kernel<T><<<dim3(nblk, 2), 128, ismem, s>>>(n, LU, lda, p->DT, p->chol);
         count_launches(1);
     }
     LU_LAUNCHED();
@@ -484,3 +520,26 @@ int getrs_f32(int n, int nrhs, const float* LU, int lda, const int* piv, float* 
 }
 
 }  // namespace lu
+
+using namespace lu;
+
+// Cholesky solve: the same work-list substitution with L and L^T.
+template <typename T>
+static int chol_solve_t(int n, int nrhs, const T* L, int lda, T* B, int ldb, cudaStream_t s) {
+    if (n < 0) return -1;
+    if (nrhs < 0 || nrhs > 384) return -2;
+    if (n > 0 && L == nullptr) return -3;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (n > 0 && nrhs > 0 && B == nullptr) return -5;
+    if (ldb < (nrhs > 1 ? nrhs : 1)) return -6;
+    return getrs_alloc<T>(n, nrhs, L, lda, nullptr, B, ldb, s);
+}
+
+extern "C" int chol_solve(int n, int nrhs, const double* L, int lda, double* B, int ldb, cudaStream_t stream) {
+    return chol_solve_t<double>(n, nrhs, L, lda, B, ldb, stream);
+}
+
+extern "C" int chol_solve_f32(int n, int nrhs, const float* L, int lda, float* B, int ldb, cudaStream_t stream) {
+    return chol_solve_t<float>(n, nrhs, L, lda, B, ldb, stream);
+}
+

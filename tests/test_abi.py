@@ -81,3 +81,18 @@ def test_chol_argument_errors_before_device_work(native):
     bad = nat.lu_opts(64, 0, nat.LU_PREC_BF16)
     assert lib.chol_factor(4, dummy, 4, dummy, ctypes.byref(bad), s) == -5
     assert lib.chol_factor_f32(4, dummy, 4, dummy, ctypes.byref(bad), s) == -5
+
+
+def test_chol_solve_argument_errors(native):
+    lib = native.library()
+    s = ctypes.c_void_p(0)
+    dummy = ctypes.c_void_p(16)
+    for fn in (lib.chol_solve, lib.chol_solve_f32):
+        assert fn(-1, 1, dummy, 1, dummy, 1, s) == -1
+        assert fn(4, -1, dummy, 4, dummy, 1, s) == -2
+        assert fn(4, 385, dummy, 4, dummy, 385, s) == -2
+        assert fn(4, 1, None, 4, dummy, 1, s) == -3
+        assert fn(4, 1, dummy, 3, dummy, 1, s) == -4
+        assert fn(4, 1, dummy, 4, None, 1, s) == -5
+        assert fn(4, 2, dummy, 4, dummy, 1, s) == -6
+        assert fn(0, 0, None, 1, None, 1, s) == 0

@@ -132,6 +132,61 @@ def test_empty_and_stream():
     assert np.abs(Lg @ Lg.T - Ah).max() <= 8 * n * 2.0 ** -53 * np.abs(Ah).max()
 
 
+EPS = 2.0 ** -53
+
+
+@pytest.mark.parametrize("dtype,eps", [(np.float64, EPS), (np.float32, 2.0 ** -24)])
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (100, 1), (257, 5), (1030, 16), (700, 40), (300, 100), (2000, 3)])
+def test_solve_against_oracle(oracle_mod, dtype, eps, n, nrhs):
+    """chol_solve with the oracle's factor: the solution within the forward
+    error bound of the oracle's substitution, and a backward error of a
+    backward-stable solve.  (The GPU applies inverted diagonal blocks, so the
+    rounding differs from plain substitution.)"""
+    torch = cuda_or_fail()
+    g = lib()
+    A = wl.matrix_spd(n, seed=n, stream=1, shift=float(n) / 4)
+    B = wl.matrix_uniform(n, nrhs, seed=n, stream=2)
+    Fo, io = oracle_mod.chol_factor(A, dtype=dtype)
+    assert io == 0
+    Xo = oracle_mod.chol_solve(Fo, B)
+    Fd = np.tril(Fo) + np.triu(np.full_like(Fo, np.nan), 1)      # upper never read
+    dL = torch.from_numpy(np.ascontiguousarray(Fd)).cuda()
+    dB = torch.from_numpy(B.astype(dtype)).cuda()
+    g.chol_solve(dL, dB)
+    torch.cuda.synchronize()
+    X = dB.cpu().numpy().astype(np.float64)
+    assert np.isfinite(X).all()
+    cond = np.linalg.cond(A)
+    assert np.abs(X - Xo).max() <= 64 * n * eps * cond * np.abs(Xo).max()
+    Ad = A.astype(dtype).astype(np.float64)
+    R = B.astype(dtype).astype(np.float64) - Ad @ X
+    eta = np.abs(R).max(axis=0) / (np.abs(Ad).sum(axis=1).max() * np.abs(X).max(axis=0) + np.abs(B).max(axis=0))
+    assert eta.max() <= 20 * n * eps
+
+
+def test_solve_vector_after_gpu_factor(oracle_mod):
+    """The public pair chol_factor -> chol_solve on a 1-D right-hand side:
+    the factor is the oracle's bit for bit, the solution within the forward
+    error bound of the oracle's."""
+    torch = cuda_or_fail()
+    g = lib()
+    n = 777
+    A = wl.matrix_spd(n, seed=5, shift=20.0)
+    b = wl.matrix_uniform(n, 1, seed=6)[:, 0]
+    dA = torch.from_numpy(A.copy()).cuda()
+    info = g.chol_factor(dA)
+    db = torch.from_numpy(b.copy()).cuda()
+    g.chol_solve(dA, db)
+    torch.cuda.synchronize()
+    assert int(info.cpu()[0]) == 0
+    Fo, _ = oracle_mod.chol_factor(A)
+    np.testing.assert_array_equal(torch.tril(dA).cpu().numpy(), np.tril(Fo))
+    xo = oracle_mod.chol_solve(Fo, b)
+    x = db.cpu().numpy()
+    assert x.shape == (n,)
+    assert np.abs(x - xo).max() <= 64 * n * EPS * np.linalg.cond(A) * np.abs(xo).max()
+
+
 # --- full size: the benchmark's configuration (n = 32768, b = 128) -----------
 
 N_FULL, B_FULL, K_FULL = 32768, 128, 2048
@@ -179,3 +234,18 @@ def test_full_size_probe(chol_full):
                     generator=torch.Generator("cuda").manual_seed(6))
     r = torch.linalg.norm(dA0 @ X - L @ (L.T @ X)) / (torch.linalg.norm(dA0) * torch.linalg.norm(X))
     assert float(r) <= 20 * N_FULL * 2.0 ** -53, float(r)
+
+
+def test_full_size_solve(chol_full):
+    """16 right-hand sides at n = 32768: normwise backward error of the solve."""
+    import torch
+    g = lib()
+    A, dA, info = chol_full
+    dA0 = torch.from_numpy(A).cuda()
+    B = torch.from_numpy(wl.matrix_uniform(N_FULL, 16, seed=9)).cuda()
+    X = B.clone()
+    g.chol_solve(dA, X)
+    torch.cuda.synchronize()
+    R = B - dA0 @ X
+    eta = R.abs().amax(0) / (dA0.abs().sum(1).amax() * X.abs().amax(0) + B.abs().amax(0))
+    assert float(eta.max()) <= 20 * N_FULL * 2.0 ** -53, float(eta.max())
