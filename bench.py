@@ -63,6 +63,8 @@ def parse():
                     help="lu64: the FP64 factorization (default line); mixed: only the mixed-precision "
                          "refinement measurement")
     ap.add_argument("--mixed-n", type=int, default=32768)
+    ap.add_argument("--chol-n", type=int, default=32768, help="order of the Cholesky measurement")
+    ap.add_argument("--chol-dtypes", default="f64,f32", help="Cholesky arithmetic(s) to measure")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision refinement measurement appended to the default line")
     return ap.parse_args()
@@ -311,16 +313,20 @@ def run_batched(a, dev, count=8192, warmup=2, steps=3):
 # ---------------------------------------------------------------------------
 # Cholesky: A = L L^T, N = 32768, symmetric Uniform[-1,1) + N I, b = 128
 # ---------------------------------------------------------------------------
-def run_cholesky(a, dev, n=32768, b=128, warmup=1, steps=2):
+def run_cholesky(a, dev, b=128, warmup=1, steps=2, nrhs=16):
     import torch
     import paper_2010_05975_gb300 as g
     import workloads as wl
+    n = a.chol_n
     flops = n ** 3 / 3.0
     out = {"n": n, "b": b, "flops": "n^3/3", "input": f"symmetric Uniform[-1,1) + n I, seed {a.seed}",
            "steps": steps, "warmup": warmup, "cases": []}
     A = wl.matrix_spd(n, seed=a.seed)
     stream = torch.cuda.current_stream(dev)
+    want = set(a.chol_dtypes.split(","))
     for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        if name not in want:
+            continue
         pristine = torch.from_numpy(A).to(dev).to(dt)
         work = torch.empty_like(pristine)
         info = torch.empty(1, dtype=torch.int32, device=dev)
@@ -342,7 +348,22 @@ def run_cholesky(a, dev, n=32768, b=128, warmup=1, steps=2):
             elif it >= warmup:
                 times.append(e0.elapsed_time(e1) / 1e3)
         t = float(np.median(times))
+        # solve with the factor: 16 right-hand sides
+        Bd = torch.ones(n, nrhs, dtype=dt, device=dev)
+        st = []
+        for it in range(3):
+            X = Bd.clone()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.chol_solve(work, X, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if it:
+                st.append(e0.elapsed_time(e1))
         case = {"dtype": name, "factor_s": t, "tflops": flops / t / 1e12, "info": int(info.cpu()[0]),
+                "solve_ms": float(np.median(st)), "solve_nrhs": nrhs,
                 "kernel_time_ms": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}
                                    for k, v in shares.items()}}
         sy = shares.get("syrk")
@@ -354,6 +375,18 @@ def run_cholesky(a, dev, n=32768, b=128, warmup=1, steps=2):
         out["cases"].append(case)
         del pristine, work
         torch.cuda.empty_cache()
+    # the oracle as it stands (single-threaded C) on a bounded sample of the
+    # same workload
+    import oracle
+    oracle.build()
+    ns = min(n, 2048)
+    As = wl.matrix_spd(ns, seed=a.seed)
+    t0 = time.perf_counter()
+    _, io = oracle.chol_factor(As)
+    tc = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": ns ** 3 / 3.0 / tc / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                           "sample": f"one binary64 oracle Cholesky of the N={ns} matrix of the same recipe "
+                                     f"({ns ** 3 / 3:.3e} flop, info {io})", "seconds": tc}
     return out
 
 
@@ -431,15 +464,20 @@ def run_serving(a, dev, rate=2000.0, count=400, pool=24, slots=6, budget=120 << 
 # ---------------------------------------------------------------------------
 def traffic_per_launch(avg_flops_per_launch: float):
     """DRAM bytes per Schur launch from the committed ncu summary, scaled by
-    algorithmic work, or None when the kernel source changed since."""
+    algorithmic work, or None when the kernel's source files (hashed in the
+    listed order) changed since."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
         rec = json.load(open(path)).get("schur_f64")
-        src = open(os.path.join(ROOT, "paper_2010_05975_gb300", "csrc", "schur_f64.cu"), "rb").read()
-        if not rec or rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        if not rec:
+            return None
+        h = hashlib.sha256()
+        for f in rec["source_files"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if rec.get("source_sha256") != h.hexdigest():
             return None
         return rec["dram_bytes_per_flop"] * avg_flops_per_launch
     except (OSError, ValueError, KeyError):

@@ -97,8 +97,13 @@ int schur_f64(double* A, int lda, int m, int k, int w, int c0, int c1, cudaStrea
 int schur_f32(float* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s);
 // Cholesky pieces (csrc/chol.cu, csrc/schur_f64.cu)
 constexpr int kCholMaxPanel = 128;      // largest Cholesky panel width
+// lower triangle of rows [c0, n) x columns [c0, c1) -= A[:, k:k+w) A[:, k:k+w)^T
 template <typename T>
 int syrk_lower(T* A, int lda, int n, int k, int w, int c0, int c1, cudaStream_t s);
+template <>
+int syrk_lower<double>(double* A, int lda, int n, int k, int w, int c0, int c1, cudaStream_t s);   // schur_f64.cu
+template <>
+int syrk_lower<float>(float* A, int lda, int n, int k, int w, int c0, int c1, cudaStream_t s);     // schur_f32.cu
 int getrs_f64(int n, int nrhs, const double* LU, int lda, const int* piv, double* B, int ldb, cudaStream_t s);
 
 // What a solve needs besides B (csrc/getrs.cu): the composed row permutation

@@ -53,10 +53,14 @@ def test_f64_bit_exact(oracle_mod, n, b, lda):
     check(oracle_mod, A, b, lda)
 
 
-@pytest.mark.parametrize("n,b", [(1, 0), (200, 64), (515, 128), (1000, 96), (1536, 128)])
-def test_f32_bit_exact(oracle_mod, n, b):
+@pytest.mark.parametrize("n,b,lda", [(1, 0, None), (200, 64, None), (515, 128, None), (1000, 96, None),
+                                     (1536, 128, None), (3000, 128, None), (2500, 100, 2503), (2200, 90, None)])
+def test_f32_bit_exact(oracle_mod, n, b, lda):
+    """From n ~ 1800 the symmetric update takes the 128 x 128 binary32 tile:
+    16-byte operand loads (n = 3000), 4-byte loads (lda = 2503) and both by
+    step (b = 90)."""
     A = wl.matrix_spd(n, seed=n + 1)
-    check(oracle_mod, A, b, dtype=np.float32)
+    check(oracle_mod, A, b, lda, dtype=np.float32)
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
@@ -144,7 +148,7 @@ def test_solve_against_oracle(oracle_mod, dtype, eps, n, nrhs):
     rounding differs from plain substitution.)"""
     torch = cuda_or_fail()
     g = lib()
-    A = wl.matrix_spd(n, seed=n, stream=1, shift=float(n) / 4)
+    A = wl.matrix_spd(n, seed=n, stream=1, shift=n / 4 + 3 * np.sqrt(n) + 1)
     B = wl.matrix_uniform(n, nrhs, seed=n, stream=2)
     Fo, io = oracle_mod.chol_factor(A, dtype=dtype)
     assert io == 0
@@ -171,7 +175,7 @@ def test_solve_vector_after_gpu_factor(oracle_mod):
     torch = cuda_or_fail()
     g = lib()
     n = 777
-    A = wl.matrix_spd(n, seed=5, shift=20.0)
+    A = wl.matrix_spd(n, seed=5, shift=100.0)
     b = wl.matrix_uniform(n, 1, seed=6)[:, 0]
     dA = torch.from_numpy(A.copy()).cuda()
     info = g.chol_factor(dA)

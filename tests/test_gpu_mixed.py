@@ -36,10 +36,13 @@ def gpu_factor_f32(A32, b, h, prec=1):
 
 
 @pytest.mark.parametrize("n,b,h", [(64, 16, 8), (300, 32, 128), (513, 64, 64), (1000, 128, 128), (250, 100, 128),
-                                   (1024, 256, 128)])
+                                   (1024, 256, 128), (2048, 256, 128), (2050, 128, 128), (1800, 90, 128)])
 def test_f32_factor_bit_exact(oracle_mod, n, b, h):
     """The all-binary32 path keeps the oracle's operation order: pivots and
-    factors equal the oracle's binary32 instance bit for bit."""
+    factors equal the oracle's binary32 instance bit for bit.  From n ~ 1700
+    the update takes the 128 x 128 binary32 tile: with 16-byte operand loads
+    (n = 2048), with 4-byte loads (n = 2050: rows not 16-byte aligned) and
+    with both by step (b = 90: panels alternately aligned)."""
     A = wl.matrix_uniform(n, n, seed=n, stream=32).astype(np.float32)
     LUg, pg, ig = gpu_factor_f32(A, b, h)
     LUo, po, io = oracle_mod.lu_factor_f32(A, b=b, h=h)
