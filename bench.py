@@ -484,6 +484,27 @@ def traffic_per_launch(avg_flops_per_launch: float):
         return None
 
 
+def reduce_over_ranks(t: float, launches: int, world: int, dev):
+    """The slowest rank's time and the kernel launches of all ranks.  The
+    ranks are independent replicas: this and the barriers are the only
+    collectives, none on the data path."""
+    if world <= 1:
+        return t, launches
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    lt = torch.tensor([launches], dtype=torch.int64, device=dev)
+    dist.all_reduce(lt)
+    dist.barrier()
+    return float(tt.item()), int(lt.item())
+
+
+def whole_job_value(world: int, steps: int, flops_per_step: float, tmax: float) -> float:
+    """TFLOP/s of the whole job: every rank's steps over the slowest rank's time."""
+    return world * steps * flops_per_step / tmax / 1e12
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -541,16 +562,8 @@ def run_ours(a):
     prof = g.prof_end()
     clk = clocks.stop()
     t = e0.elapsed_time(e1) / 1e3
-    tmax = t
-    if world > 1:
-        tt = torch.tensor([t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tmax = float(tt.item())
-        lt = torch.tensor([launches], dtype=torch.int64, device=dev)
-        dist.all_reduce(lt)
-        launches = int(lt.item())
-        dist.barrier()
-    value = world * a.steps * flops / tmax / 1e12
+    tmax, launches = reduce_over_ranks(t, launches, world, dev)
+    value = whole_job_value(world, a.steps, flops, tmax)
 
     # end to end through the host-buffer public call
     hout = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
@@ -566,11 +579,8 @@ def run_ours(a):
     f1.record(stream)
     torch.cuda.synchronize(dev)
     te = f0.elapsed_time(f1) / 1e3
-    if world > 1:
-        tt = torch.tensor([te], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
-    e2e = {"value": world * ke * flops / te / 1e12, "unit": UNIT, "steps": ke,
+    te, _ = reduce_over_ranks(te, 0, world, dev)
+    e2e = {"value": whole_job_value(world, ke, flops, te), "unit": UNIT, "steps": ke,
            "h2d_bytes_per_step": int(hA.numel() * 8),
            "d2h_bytes_per_step": int(hout.numel() * 8 + piv_h.numel() * 4 + 4)}
 
