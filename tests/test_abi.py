@@ -96,3 +96,15 @@ def test_chol_solve_argument_errors(native):
         assert fn(4, 1, dummy, 4, None, 1, s) == -5
         assert fn(4, 2, dummy, 4, dummy, 1, s) == -6
         assert fn(0, 0, None, 1, None, 1, s) == 0
+
+
+def test_python_cholesky_refuses_bad_tensors(native):
+    import torch
+    with pytest.raises(TypeError):
+        native.chol_factor(torch.zeros(4, 4, dtype=torch.float64))          # host tensor
+    with pytest.raises(TypeError):
+        native.chol_factor(torch.zeros(4, 4, dtype=torch.int32))
+    with pytest.raises(TypeError):
+        native.chol_solve(torch.zeros(4, 4, dtype=torch.float16), torch.zeros(4))
+    with pytest.raises(TypeError):
+        native.chol_solve(torch.zeros(4, 4, dtype=torch.float64), torch.zeros(4, dtype=torch.float64))
