@@ -151,3 +151,40 @@ def test_lowp_factor_against_oracle(oracle_mod, prec, n, b):
     np.testing.assert_array_equal(pg[:b], po[:b])
     rg, ro = _residual(A, LUg, pg), _residual(A, LUo, po)
     assert 0.5 * ro <= rg <= 2.0 * ro, (rg, ro)
+
+
+# --- closed forms: the mixed-precision factorization bit for bit ------------
+
+from tests import lowp_closed_form as cf  # noqa: E402
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("n,b,h", [(1100, 128, 128), (1100, 256, 128), (777, 128, 64)])
+def test_lowp_factor_exact_closed_form_bitwise(oracle_mod, prec, n, b, h):
+    """Operands exact in bf16 / e4m3 and partial sums exact in binary32:
+    whatever order the tensor cores add in, the GPU returns P = I and the
+    closed-form L and U bit for bit, as the oracle does."""
+    A, LU = cf.exact_factors(n)
+    LUg, pg, ig = gpu_factor_f32(A, b, h, prec=prec)
+    assert ig == 0
+    np.testing.assert_array_equal(pg, np.arange(n))
+    np.testing.assert_array_equal(LUg, LU)
+    LUo, po, io = oracle_mod.lu_factor_f32(A, b=b, h=h, lowp=prec - 1)
+    np.testing.assert_array_equal(LUg, LUo)
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("b", [128, 256])
+def test_lowp_factor_rounded_first_update_bitwise(oracle_mod, prec, b):
+    """The first tensor-core update rounds L21 and U12 (bf16, or e4m3 with the
+    step's tile scales, some values on the subnormal grid); its result is
+    exact in binary32, so the trailing block must come out as the diagonal D
+    and the factors as the closed form, bit for bit."""
+    n = b + 600
+    A, LU = cf.rounded_first_update(n, b, prec == 3)
+    LUg, pg, ig = gpu_factor_f32(A, b, 128, prec=prec)
+    assert ig == 0
+    np.testing.assert_array_equal(pg, np.arange(n))
+    np.testing.assert_array_equal(LUg, LU)
+    LUo, po, io = oracle_mod.lu_factor_f32(A, b=b, h=128, lowp=prec - 1)
+    np.testing.assert_array_equal(LUg, LUo)

@@ -95,3 +95,57 @@ def test_f32_closed_form_exact(oracle_mod):
     np.testing.assert_array_equal(piv, np.arange(n))
     np.testing.assert_array_equal(np.tril(LU, -1) + np.eye(n), L.astype(np.float32))
     np.testing.assert_array_equal(np.triu(LU), U.astype(np.float32))
+
+
+# --- the mixed-precision factorization (Section 7.2 FactorizeA11 with the
+# low-precision operands of the mixed-precision reading), pinned by closed
+# forms whose factors are known before the factorization runs --------------
+
+from tests import lowp_closed_form as cf  # noqa: E402
+
+
+@pytest.mark.parametrize("lowp", [1, 2])
+@pytest.mark.parametrize("n,b,h", [(1100, 128, 128), (1100, 256, 128), (777, 128, 64)])
+def test_lowp_factor_exact_closed_form(oracle_mod, lowp, n, b, h):
+    """A = L U whose operands are exact in bf16 and e4m3 and whose partial
+    sums are exact in binary32: every step is exact, so P = I and the factors
+    are L and U bit for bit.  Row / column classes 4x apart make a value that
+    takes another tile's fp8 scale saturate, so a misplaced scale fails."""
+    A, LU = cf.exact_factors(n)
+    LUo, po, io = oracle_mod.lu_factor_f32(A, b=b, h=h, lowp=lowp)
+    assert io == 0
+    np.testing.assert_array_equal(po, np.arange(n))
+    np.testing.assert_array_equal(LUo, LU)
+
+
+@pytest.mark.parametrize("fp8", [False, True])
+@pytest.mark.parametrize("b", [128, 256])
+def test_lowp_factor_rounds_first_update(oracle_mod, fp8, b):
+    """The first Schur update must subtract exactly q(L21) q(U12) (torch's
+    roundings, scale tiles counted from the first trailing row / column):
+    then the trailing block is the diagonal D and the factors are known.  The
+    plain binary32 factorization of the same matrix does not give them."""
+    n = b + 600
+    A, LU = cf.rounded_first_update(n, b, fp8)
+    LUo, po, io = oracle_mod.lu_factor_f32(A, b=b, h=128, lowp=2 if fp8 else 1)
+    assert io == 0
+    np.testing.assert_array_equal(po, np.arange(n))
+    np.testing.assert_array_equal(LUo, LU)
+    LUf, pf, _ = oracle_mod.lu_factor_f32(A, b=b, h=128)
+    assert not np.array_equal(LUf, LU)
+
+
+def test_rounded_update_tells_tile_origins_apart():
+    """With b = 128 the step's tiles start at row / column 128; tiles counted
+    from row / column 0 put other rows beside the large values, round them
+    differently and leave a nonzero off-diagonal trailing block."""
+    W = cf.rounded_first_update_wrong_origin(728, 128)
+    off = W - np.diag(np.diag(W))
+    assert np.count_nonzero(off) > 1000
+
+
+def test_closed_form_exponents_match_oracle_rule(oracle_mod):
+    """The tile exponents of the closed forms follow the oracle's binary32
+    decision on these tiles (the exact rule and the binary32 one agree)."""
+    for v in (0.4995, 0.125, 2.0 ** -15 * 1.9, 1.999, 448.0, 449.0, 3.0):
+        assert cf.e4m3_exponent_exact(v) == oracle_mod.e4m3_exponent(np.float32(v))
