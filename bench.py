@@ -42,6 +42,20 @@ UNIT = "TFLOP/s"
 # binary64 peak of the DFMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 # (the nominal 1.25 TFLOP/s per GPU at the maximum SM clock).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# fallback HBM copy bandwidth when no measured peak file is present
+HBM_FALLBACK_GBS = 6800.0
+
+
+def measured_peaks():
+    """(hbm GB/s, bf16 TFLOP/s burst, source) from MEASURED_PEAKS.json (the
+    pool's measured STREAM-style copy and cuBLAS bf16 GEMM), else the
+    fallback figures."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return HBM_FALLBACK_GBS, 1900.0, "fallback"
 
 
 def parse():
@@ -59,9 +73,15 @@ def parse():
     ap.add_argument("--ref-sample-n", type=int, default=4096,
                     help="order of the matrix the CPU oracle factors in each --impl reference step")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=["lu64", "mixed", "batched", "serving", "cholesky"], default="lu64",
+    ap.add_argument("--workload", choices=["lu64", "mixed", "batched", "serving", "cholesky", "lowp_gemm",
+                                           "lowp_factor"],
+                    default="lu64",
                     help="lu64: the FP64 factorization (default line); mixed: only the mixed-precision "
-                         "refinement measurement")
+                         "refinement measurement; lowp_gemm: the tensor-core Schur update alone")
+    ap.add_argument("--lowp-n", type=int, default=16384, help="M = N of the lowp_gemm workload")
+    ap.add_argument("--lowp-k", type=int, default=256, help="K of the lowp_gemm workload")
+    ap.add_argument("--lowp-prec", default="bf16,fp8", help="operand formats of the lowp_gemm / lowp_factor workloads")
+    ap.add_argument("--defers", default="1,2,4", help="deferrals measured by the lowp_factor workload")
     ap.add_argument("--mixed-n", type=int, default=32768)
     ap.add_argument("--chol-n", type=int, default=32768, help="order of the Cholesky measurement")
     ap.add_argument("--chol-dtypes", default="f64,f32", help="Cholesky arithmetic(s) to measure")
@@ -251,7 +271,8 @@ def run_mixed(a, dev, t_fp64_factor=None, warmup=1, steps=2, kappas=(1e2, 1e4, 1
                     "iters": res["iters"], "gmres_iters": res["gmres_iters"], "path": res["path"],
                     "final_precision": ["f64", "f32", "bf16", "fp8"][res["precision"]],
                     "eta": res["eta"], "fwd_err": fwd,
-                    "kernel_ms": {k: round(v["ms"], 2) for k, v in prof.items()}}
+                    "kernel_ms": {k: round(v["ms"], 2) for k, v in prof.items()},
+                    "roofline_schur_lowp": lowp_roofline(prof.get("schur_lowp"), f"schur_tc_{pname}")}
             if t_fp64_factor is not None:
                 case["speedup_vs_fp64_solve"] = (t_fp64_factor + t_solve64) / t
             out["cases"].append(case)
@@ -460,18 +481,121 @@ def run_serving(a, dev, rate=2000.0, count=400, pool=24, slots=6, budget=120 << 
 
 
 # ---------------------------------------------------------------------------
+# the tensor-core Schur update alone: C (M x N, fp32) -= q(L) q(U), K = 256
+# ---------------------------------------------------------------------------
+def lowp_roofline(entry: dict, traffic_key: str | None = None):
+    """HBM roofline of the tcgen05 update from its launch records: the
+    algorithmic bytes (fp32 C read and written once, quantized operands read
+    once) per event-timed second, against the measured copy bandwidth."""
+    if not entry or not entry.get("launches") or entry["ms"] <= 0:
+        return None
+    hbm, _, src = measured_peaks()
+    ach = entry["bytes"] / (entry["ms"] / 1e3) / 1e9
+    out = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+           "peak_source": src, "kernel": "schur_tc_kernel", "launches": entry["launches"],
+           "avg_launch_ms": entry["ms"] / entry["launches"],
+           "tflops": entry["flops"] / (entry["ms"] / 1e3) / 1e12,
+           "traffic": None}
+    if traffic_key:
+        rec = traffic_record(traffic_key)
+        if rec is not None:
+            out["traffic"] = rec * entry["bytes"] / entry["launches"]
+    return out
+
+
+def run_lowp_factor(a, dev, warmup=1):
+    """The bf16 / fp8 factorization alone (binary32 matrix of the mixed
+    workload's Householder construction, kappa = 1e2) at several deferrals:
+    time, kernel shares and the tcgen05 update's roofline."""
+    import torch
+    import paper_2010_05975_gb300 as g
+    n = a.mixed_n
+    A64 = householder_on_device(n, 1e2, 2, dev)
+    A0 = A64.to(torch.float32)
+    del A64
+    torch.cuda.empty_cache()
+    A = torch.empty_like(A0)
+    stream = torch.cuda.current_stream(dev)
+    out = {"n": n, "b": 128, "h": 128, "cases": []}
+    for name in a.lowp_prec.split(","):
+        prec = {"bf16": g.LU_PREC_BF16, "fp8": g.LU_PREC_FP8}[name]
+        for d in [int(x) for x in a.defers.split(",")]:
+            times = []
+            for it in range(warmup + a.steps):
+                A.copy_(A0)
+                torch.cuda.synchronize(dev)
+                prof = it == warmup + a.steps - 1
+                if prof:
+                    g.prof_begin()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                piv, info = g.lu_factor_f32(A, b=128, h=128, precision=prec, stream=stream, defer=d)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                if prof:
+                    pr = g.prof_end()
+                if it >= warmup:
+                    times.append(e0.elapsed_time(e1))
+            if int(info.cpu()[0]) != 0:
+                raise RuntimeError(f"lowp factorization info={int(info.cpu()[0])}")
+            out["cases"].append({"precision": name, "defer": d, "ms": float(np.median(times)),
+                                 "tflops": 2.0 * n ** 3 / 3.0 / (np.median(times) / 1e3) / 1e12,
+                                 "kernel_ms": {k: {"launches": v["launches"], "ms": round(v["ms"], 2)}
+                                               for k, v in pr.items()},
+                                 "roofline_schur_lowp": lowp_roofline(pr.get("schur_lowp"), f"schur_tc_{name}")})
+    return out
+
+
+def run_lowp_gemm(a, dev, warmup=3):
+    import torch
+    import paper_2010_05975_gb300 as g
+    M = N = a.lowp_n
+    K = a.lowp_k
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(a.seed)
+    L = torch.randn(M, K, dtype=torch.float32, device=dev, generator=gen)
+    U = torch.randn(K, N, dtype=torch.float32, device=dev, generator=gen)
+    C0 = torch.randn(M, N, dtype=torch.float32, device=dev, generator=gen)
+    C = torch.empty_like(C0)
+    stream = torch.cuda.current_stream(dev)
+    out = {"M": M, "N": N, "K": K, "steps": a.steps, "warmup": warmup,
+           "l2_flush": f"C is {M * N * 4 / 1e9:.2f} GB, larger than L2", "cases": []}
+    for name in a.lowp_prec.split(","):
+        prec = {"bf16": g.LU_PREC_BF16, "fp8": g.LU_PREC_FP8}[name]
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        for _ in range(warmup):
+            C.copy_(C0)
+            g.lu_gemm_lowp(L, U, C, precision=prec, status=st, stream=stream)
+        torch.cuda.synchronize(dev)
+        g.prof_begin()
+        for _ in range(a.steps):
+            C.copy_(C0)
+            g.lu_gemm_lowp(L, U, C, precision=prec, status=st, stream=stream)
+        torch.cuda.synchronize(dev)
+        prof = g.prof_end()
+        if int(st.cpu()[0]) != 0:
+            raise RuntimeError(f"tcgen05 update reported status {int(st.cpu()[0])}")
+        out["cases"].append({"precision": name,
+                             "roofline": lowp_roofline(prof.get("schur_lowp"), f"schur_tc_{name}"),
+                             "kernel_ms": {k: round(v["ms"] / a.steps, 4) for k, v in prof.items()}})
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
-def traffic_per_launch(avg_flops_per_launch: float):
-    """DRAM bytes per Schur launch from the committed ncu summary, scaled by
-    algorithmic work, or None when the kernel's source files (hashed in the
-    listed order) changed since."""
+def traffic_record(key: str):
+    """DRAM bytes per unit of algorithmic work (flop, or algorithmic byte)
+    of one kernel from the committed ncu summary (profiles/traffic.json), or
+    None when the kernel's source files (hashed in the listed order) changed
+    since the counters were taken."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
-        rec = json.load(open(path)).get("schur_f64")
+        rec = json.load(open(path)).get(key)
         if not rec:
             return None
         h = hashlib.sha256()
@@ -479,9 +603,15 @@ def traffic_per_launch(avg_flops_per_launch: float):
             h.update(open(os.path.join(ROOT, f), "rb").read())
         if rec.get("source_sha256") != h.hexdigest():
             return None
-        return rec["dram_bytes_per_flop"] * avg_flops_per_launch
+        return rec.get("dram_bytes_per_flop", rec.get("dram_bytes_per_alg_byte"))
     except (OSError, ValueError, KeyError):
         return None
+
+
+def traffic_per_launch(avg_flops_per_launch: float):
+    """DRAM bytes per binary64 Schur launch, scaled by its algorithmic work."""
+    r = traffic_record("schur_f64")
+    return None if r is None else r * avg_flops_per_launch
 
 
 def reduce_over_ranks(t: float, launches: int, world: int, dev):
@@ -565,24 +695,30 @@ def run_ours(a):
     tmax, launches = reduce_over_ranks(t, launches, world, dev)
     value = whole_job_value(world, a.steps, flops, tmax)
 
-    # end to end through the host-buffer public call
-    hout = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    # end to end through the C ABI's host-buffer call lu_factor_host: each
+    # step copies the matrix in from pinned host memory, factors it and
+    # copies L\\U, the pivots and info back (host wall time of the call; the
+    # pristine input is restored into the work buffer between calls, outside
+    # the timed call)
+    hwork = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
     ke = max(1, a.e2e_steps)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
+    te = 0.0
     for _ in range(ke):
-        _, piv_h, info_h = g.lu_factor_host(hA, b=b, h=h, out=hout, device=dev, stream=stream)
-    f1.record(stream)
-    torch.cuda.synchronize(dev)
-    te = f0.elapsed_time(f1) / 1e3
+        hwork.copy_(hA)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        piv_h, info_h = g.lu_factor_host(hwork, b=b, h=h, stream=stream)
+        te += time.perf_counter() - t0
+        if info_h != 0:
+            raise RuntimeError(f"lu_factor_host reported info={info_h}")
     te, _ = reduce_over_ranks(te, 0, world, dev)
     e2e = {"value": whole_job_value(world, ke, flops, te), "unit": UNIT, "steps": ke,
-           "h2d_bytes_per_step": int(hA.numel() * 8),
-           "d2h_bytes_per_step": int(hout.numel() * 8 + piv_h.numel() * 4 + 4)}
+           "call": "lu_factor_host (C ABI, pinned host buffers)",
+           "h2d_bytes_per_step": int(n * n * 8),
+           "d2h_bytes_per_step": int(n * n * 8 + piv_h.numel() * 4 + 4)}
+    del hwork
 
     sch = prof.get("schur_f64", {"launches": 0, "ms": 0.0, "flops": 0.0})
     roof = None
@@ -633,7 +769,7 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    elif a.workload in ("mixed", "batched", "serving", "cholesky"):
+    elif a.workload in ("mixed", "batched", "serving", "cholesky", "lowp_gemm", "lowp_factor"):
         import torch
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
         torch.cuda.set_device(dev)
@@ -642,6 +778,12 @@ def main():
         if a.workload == "mixed":
             print(json.dumps({"metric": "IR solves/s at 1e-12 backward error", "unit": "solves/s",
                               "mixed_ir": run_mixed(a, dev)}), flush=True)
+        elif a.workload == "lowp_factor":
+            print(json.dumps({"metric": "mixed-precision LU TFLOP/s (2N^3/3)", "unit": "TFLOP/s",
+                              "lowp_factor": run_lowp_factor(a, dev)}), flush=True)
+        elif a.workload == "lowp_gemm":
+            print(json.dumps({"metric": "tcgen05 Schur update HBM GB/s", "unit": "GB/s",
+                              "lowp_gemm": run_lowp_gemm(a, dev)}), flush=True)
         elif a.workload == "cholesky":
             print(json.dumps({"metric": "Cholesky TFLOP/s (N^3/3)", "unit": "TFLOP/s",
                               "cholesky": run_cholesky(a, dev)}), flush=True)

@@ -72,7 +72,11 @@ typedef struct {
     int h;                  /* tournament leaf height: rows per leaf of the
                                first round (Section 7.3); default 128          */
     int precision;          /* lu_precision; default LU_PREC_F64               */
-    int reserved[5];        /* must be zero                                     */
+    int defer;              /* BF16 / FP8 factorization only: panels whose
+                               trailing updates are held back and applied in
+                               one pass over the trailing matrix (1..4;
+                               0 = 4); the factors do not depend on it       */
+    int reserved[4];        /* must be zero                                     */
 } lu_opts;
 
 /*
@@ -93,7 +97,8 @@ int lu_factor(int n, double *A, int lda, int *piv, int *info, cudaStream_t strea
  * lu_factor_ex -- rectangular m x n factorization with options.  min(m, n)
  * pivots are produced; for m < n the result is L (m x m) and an upper
  * trapezoidal U (m x n).  opts may be NULL (defaults).  Only LU_PREC_F64 is
- * accepted here; the mixed-precision factorization lives in lu_factor_mixed.
+ * accepted here; the binary32 and mixed-precision factorizations are
+ * lu_factor_f32 with opts->precision F32, BF16 or FP8.
  * Tournament nodes hold up to max(leaf rows, 2b) x b panel values in the
  * shared memory of one thread-block cluster: b <= 256 and
  * max(h', 2b) * b <= 204800 where h' is the first tree level's row count.
@@ -102,10 +107,34 @@ int lu_factor_ex(int m, int n, double *A, int lda, int *piv, int *info,
                  const lu_opts *opts, cudaStream_t stream);
 
 /*
- * lu_solve -- X = U^{-1} L^{-1} P B with the factors of lu_factor.
+ * lu_factor_host -- lu_factor_ex on a matrix in HOST memory: the call copies
+ * A to the device, factors it there (Algorithm 1, binary64) and copies L\U,
+ * the pivots and info back, then returns with the results in host memory
+ * (it synchronizes `stream`).
+ *   m, n, lda, opts  as lu_factor_ex (opts->precision must be 0 or F64)
+ *   A     HOST, m x n row-major; overwritten by L and U.  Page-locked memory
+ *         (cudaHostAlloc / cudaHostRegister) lets the copies run at the
+ *         link's rate; pageable memory works, more slowly.
+ *   piv   HOST int[min(m, n)]
+ *   info  HOST int
+ * Device memory: one m x n binary64 buffer plus the factorization's
+ * workspace, taken from the stream-ordered allocator and returned before the
+ * call returns.  Returns 0, -i for an invalid argument i, LU_ENOMEM,
+ * LU_ELAUNCH, or LU_EUNSUPPORTED for a precision other than binary64.
+ */
+int lu_factor_host(int m, int n, double *A, int lda, int *piv, int *info,
+                   const lu_opts *opts, cudaStream_t stream);
+
+/*
+ * lu_solve -- X = U^{-1} L^{-1} P B with the factors of lu_factor: the
+ * linear-system solve that the factorization exists for (the paper names
+ * linear solvers as LU's use in Section 1 and does not spell the solve out;
+ * this is LAPACK getrs's forward and backward substitution).
  *   n, LU, lda, piv  as returned by lu_factor (device)
- *   nrhs  number of right-hand sides, nrhs >= 0
+ *   nrhs  number of right-hand sides, 0 <= nrhs <= 384
  *   B     device, n x nrhs row-major, ldb >= max(1, nrhs); overwritten by X
+ * Returns 0, -i for an invalid argument i, or LU_ENOMEM / LU_ELAUNCH /
+ * LU_ETIMEOUT (a bounded device wait ran out; B is then invalid).
  */
 int lu_solve(int n, int nrhs, const double *LU, int lda, const int *piv,
              double *B, int ldb, cudaStream_t stream);
@@ -214,9 +243,10 @@ int lu_residual(int n, int nrhs, const double *A, int lda, const double *X,
  * (larger nrhs returns -2 before any work).  It calls no cudaMalloc,
  * cudaFree or other allocating routine.  Its reduction scratch is one fixed
  * array of about 160 KB per device, placed in the library and kept until the
- * process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first
- * call before any stream capture.  Every call on a device uses the same
+ * process exits.  Each call looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current, so a device reset between
+ * calls leaves no stale address behind; the first call on a device may load
+ * the library's device code, so make it before any stream capture.  Every call on a device uses the same
  * array, so calls whose work overlaps on the GPU (different streams, no
  * ordering between them) race and give wrong results; calls ordered on one
  * stream are safe.  Nothing in the array has to start at zero: each call
@@ -228,8 +258,11 @@ int lu_residual_noalloc(int n, int nrhs, const double *A, int lda,
 
 /*
  * lu_factor_batched -- factor `batch` independent square matrices in one
- * persistent launch (the same tournament-pivoting LU as lu_factor, one CTA
- * per matrix, largest matrices scheduled first).
+ * persistent launch: Algorithm 1 (TournPivot of Section 7.3, then
+ * FactorizeA10 / A01 / A11 of Section 7.2) run per matrix by one CTA, the
+ * largest matrices scheduled first.  Each matrix's pivots and factors are
+ * those of lu_factor_ex with the same b and h, whatever else is in the
+ * batch.
  *   n, lda  device int[batch]: order (0 <= n <= 1024) and leading dimension
  *   A       device array of batch device pointers (double* or float*)
  *   piv     device array of batch device pointers to int[n]
@@ -411,6 +444,38 @@ int lu_prof_begin(void);
 int lu_prof_end(lu_prof_entry *out, int max_entries, int *n_entries);
 /* Kernels launched by this library in this process so far. */
 unsigned long long lu_kernel_launch_count(void);
+
+/* ---------------------------------------------------------------------------
+ * Bounded device waits (no counterpart in the paper).  The library's kernels
+ * wait on each other's progress in two places: the tensor-core Schur update
+ * (mbarrier waits between its copy, MMA and epilogue warps) and the
+ * work-list triangular solve (a work item waits for the items it depends
+ * on).  Each such wait gives up after a wall-clock deadline (default 4 s,
+ * read on the device from %globaltimer); the kernel then stops taking work,
+ * waits for its own copies and MMAs in flight, frees its tensor memory and
+ * exits, and the call reports LU_ETIMEOUT (the factorizations through
+ * *info = -LU_ETIMEOUT, the solves through their return value).
+ * ------------------------------------------------------------------------- */
+#define LU_WAIT_SITE_TC     0   /* tcgen05 Schur update (lu_gemm_lowp, the
+                                   bf16 / fp8 factorization, ir_solve)          */
+#define LU_WAIT_SITE_SOLVE  1   /* work-list triangular solves                  */
+#define LU_WAIT_NSITES      2
+
+/*
+ * lu_test_wait_config -- TEST HOOK: set the dependency-wait deadline of one
+ * wait site (wait_ns > 0; 0 restores the 4 s default) and, with inject = 1,
+ * make every later launch at that site first wait once on something that is
+ * never signalled (an mbarrier nothing arrives on; a counter nothing
+ * increments), so that the wait runs out after wait_ns and the error path
+ * runs without a device fault.  Process-wide; applies to launches made after
+ * the call.  Returns 0, -1 bad site, -2 wait_ns < 0 or > 600 s, -3 inject
+ * not 0 or 1.
+ */
+int lu_test_wait_config(int site, long long wait_ns, int inject);
+
+/* The deadline in nanoseconds that launches at `site` use now, or -1 for a
+ * bad site. */
+long long lu_wait_deadline_ns(int site);
 
 #ifdef __cplusplus
 }

@@ -17,6 +17,8 @@ from ._native import (  # noqa: F401
     LU_PREC_F32,
     LU_PREC_BF16,
     LU_PREC_FP8,
+    LU_WAIT_SITE_TC,
+    LU_WAIT_SITE_SOLVE,
     LuError,
     library,
     library_path,
@@ -41,4 +43,5 @@ from .api import (  # noqa: F401
     prof_begin,
     prof_end,
     kernel_launch_count,
+    set_wait_config,
 )

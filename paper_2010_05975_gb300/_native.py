@@ -14,6 +14,9 @@ LU_EBUSY = 4
 LU_EUNSUPPORTED = 5
 LU_ENOTFOUND = 6
 
+LU_WAIT_SITE_TC = 0
+LU_WAIT_SITE_SOLVE = 1
+
 LU_PREC_F64 = 0
 LU_PREC_F32 = 1
 LU_PREC_BF16 = 2
@@ -31,8 +34,8 @@ class LuError(RuntimeError):
 
 
 class lu_opts(ctypes.Structure):
-    _fields_ = [("b", ctypes.c_int), ("h", ctypes.c_int), ("precision", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+    _fields_ = [("b", ctypes.c_int), ("h", ctypes.c_int), ("precision", ctypes.c_int), ("defer", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class ir_opts(ctypes.Structure):
@@ -96,6 +99,7 @@ I = ctypes.c_int
 _SIGS = {
     "lu_factor": ([I, P, I, P, P, P], I),
     "lu_factor_ex": ([I, I, P, I, P, P, ctypes.POINTER(lu_opts), P], I),
+    "lu_factor_host": ([I, I, P, I, P, P, ctypes.POINTER(lu_opts), P], I),
     "lu_solve": ([I, I, P, I, P, P, I, P], I),
     "lu_factor_f32": ([I, I, P, I, P, P, ctypes.POINTER(lu_opts), P], I),
     "lu_solve_f32": ([I, I, P, I, P, P, I, P], I),
@@ -118,6 +122,8 @@ _SIGS = {
     "lu_prof_begin": ([], I),
     "lu_prof_end": ([P, I, P], I),
     "lu_kernel_launch_count": ([], ctypes.c_ulonglong),
+    "lu_test_wait_config": ([I, ctypes.c_longlong, I], I),
+    "lu_wait_deadline_ns": ([I], ctypes.c_longlong),
 }
 
 

@@ -96,37 +96,41 @@ def kernel_launch_count() -> int:
     return int(nat.library().lu_kernel_launch_count())
 
 
-def lu_factor_host(A_host: torch.Tensor, b: int = 0, h: int = 0, out: torch.Tensor | None = None,
-                   device: torch.device | str | None = None, stream=None):
-    """Factor a matrix that lives in host memory: copy it to the device, run
-    lu_factor_ex there, copy L\\U and the pivots back.  A_host is a row-major
-    float64 CPU tensor (pinned memory makes the copies asynchronous); the
-    result goes to `out` (a CPU tensor, allocated when None).  Returns
-    (out, piv_host, info)."""
-    if A_host.is_cuda or A_host.dtype != torch.float64 or A_host.dim() != 2:
-        raise TypeError("A_host must be a 2-D float64 CPU tensor")
-    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+def lu_factor_host(A_host: torch.Tensor, b: int = 0, h: int = 0, piv: torch.Tensor | None = None,
+                   stream=None):
+    """In-place factorization of a matrix in host memory through the C ABI's
+    lu_factor_host (copy in, factor on the device, copy L\\U and the pivots
+    back; returns when they are in host memory).  A_host is a row-major
+    float64 CPU tensor, overwritten by L and U; page-locked memory
+    (pin_memory()) makes the copies run at the link's rate.  Returns
+    (piv, info) with piv an int32 CPU tensor."""
+    if A_host.is_cuda or A_host.dtype != torch.float64 or A_host.dim() != 2 or A_host.stride(1) != 1:
+        raise TypeError("A_host must be a row-major 2-D float64 CPU tensor")
     m, n = A_host.shape
-    s = stream if stream is not None else torch.cuda.current_stream(dev)
-    with torch.cuda.stream(s):
-        dA = torch.empty((m, n), dtype=torch.float64, device=dev)
-        dA.copy_(A_host, non_blocking=True)
-        piv, info = lu_factor_ex(dA, b=b, h=h, stream=s)
-        if out is None:
-            out = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
-        out.copy_(dA, non_blocking=True)
-        piv_h = torch.empty(piv.shape, dtype=torch.int32, pin_memory=True)
-        info_h = torch.empty(1, dtype=torch.int32, pin_memory=True)
-        piv_h.copy_(piv, non_blocking=True)
-        info_h.copy_(info, non_blocking=True)
-    s.synchronize()
-    return out, piv_h, int(info_h[0])
+    k = min(m, n)
+    if piv is None:
+        piv = torch.empty(max(k, 1), dtype=torch.int32, pin_memory=A_host.is_pinned())
+    info = ctypes.c_int(0)
+    opts = nat.lu_opts(b, h, nat.LU_PREC_F64)
+    rc = nat.library().lu_factor_host(m, n, A_host.data_ptr(), max(A_host.stride(0), 1), piv.data_ptr(),
+                                      ctypes.byref(info), ctypes.byref(opts), _stream_handle(stream))
+    nat.check("lu_factor_host", rc)
+    return piv[:k], info.value
+
+
+def set_wait_config(site: int, wait_ns: int = 0, inject: int = 0) -> None:
+    """Test hook: deadline of one wait site's dependency waits (0 = the 4 s
+    default) and whether launches there first wait on something never
+    signalled, so that the wait runs out (see lu_test_wait_config)."""
+    nat.check("lu_test_wait_config", nat.library().lu_test_wait_config(int(site), int(wait_ns), int(inject)))
 
 
 def lu_factor_f32(A: torch.Tensor, b: int = 0, h: int = 0, precision: int = nat.LU_PREC_F32,
-                  piv: torch.Tensor | None = None, info: torch.Tensor | None = None, stream=None):
+                  piv: torch.Tensor | None = None, info: torch.Tensor | None = None, stream=None,
+                  defer: int = 0):
     """In-place factorization of a float32 CUDA matrix.  precision selects the
-    Schur-update operands: F32, BF16 or FP8 (tensor cores)."""
+    Schur-update operands: F32, BF16 or FP8 (tensor cores); defer (BF16 / FP8
+    only) how many panels' trailing updates one pass applies (0 = default)."""
     _require(A, "A", torch.float32, 2)
     m, n = A.shape
     k = min(m, n)
@@ -134,7 +138,7 @@ def lu_factor_f32(A: torch.Tensor, b: int = 0, h: int = 0, precision: int = nat.
         piv = torch.empty(max(k, 1), dtype=torch.int32, device=A.device)
     if info is None:
         info = torch.empty(1, dtype=torch.int32, device=A.device)
-    opts = nat.lu_opts(b, h, precision)
+    opts = nat.lu_opts(b, h, precision, defer)
     rc = nat.library().lu_factor_f32(m, n, A.data_ptr(), max(A.stride(0), 1), piv.data_ptr(), info.data_ptr(),
                                      ctypes.byref(opts), _stream_handle(stream))
     nat.check("lu_factor_f32", rc)
@@ -248,6 +252,18 @@ def ir_solve(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor | None = None, pr
     return X, out
 
 
+def _keep_for_stream(stream, *tensors):
+    """The size and pointer arrays are made on the current stream and freed
+    when this call returns; the caching allocator hands their memory out again
+    only to work ordered after them on that stream.  When the launch went to
+    another stream, record that stream on them so that their memory is not
+    reused before the launch has read them."""
+    if stream is None or stream == torch.cuda.current_stream(tensors[0].device):
+        return
+    for t in tensors:
+        t.record_stream(stream)
+
+
 def _ptr_array(tensors, device):
     return torch.tensor([t.data_ptr() for t in tensors], dtype=torch.int64, device=device)
 
@@ -277,8 +293,7 @@ def lu_factor_batched(As, stream=None):
     rc = nat.library().lu_factor_batched(len(As), n.data_ptr(), pa.data_ptr(), lda.data_ptr(), pp.data_ptr(),
                                          info.data_ptr(), prec, _stream_handle(stream))
     nat.check("lu_factor_batched", rc)
-    # the pointer and size arrays must outlive the launch
-    lu_factor_batched._keep = (n, lda, pa, pp)
+    _keep_for_stream(stream, n, lda, pa, pp)
     return [p[: A.shape[0]] for p, A in zip(pivs, As)], info
 
 
@@ -298,7 +313,7 @@ def lu_solve_batched(LUs, pivs, Bs, stream=None):
     rc = nat.library().lu_solve_batched(len(LUs), n.data_ptr(), nr.data_ptr(), pl.data_ptr(), lda.data_ptr(),
                                         pp.data_ptr(), pb.data_ptr(), ldb.data_ptr(), prec, _stream_handle(stream))
     nat.check("lu_solve_batched", rc)
-    lu_solve_batched._keep = (n, nr, lda, ldb, pl, pp, pb)
+    _keep_for_stream(stream, n, nr, lda, ldb, pl, pp, pb)
     return Bs
 
 

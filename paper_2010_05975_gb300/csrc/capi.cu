@@ -132,7 +132,7 @@ static int factor_loop(int m, int n, T* A, int lda, int* piv, int* info, int b, 
 // Shared argument checks of the factor entry points.  Returns 0 and fills
 // b, h, prec, or a negative argument index.
 static int factor_args(int m, int n, const void* A, int lda, const int* piv, const int* info, const lu_opts* opts,
-                       int elem, int& b, int& h, int& prec) {
+                       int elem, int& b, int& h, int& prec, int* defer = nullptr) {
     if (m < 0) return -1;
     if (n < 0) return -2;
     if (lda < (n > 1 ? n : 1)) return -4;
@@ -143,8 +143,11 @@ static int factor_args(int m, int n, const void* A, int lda, const int* piv, con
     b = (n >= 4096) ? 256 : 32;
     h = 128;
     prec = (elem == 8) ? LU_PREC_F64 : LU_PREC_F32;
+    if (defer) *defer = 0;
     if (opts) {
         if (opts->b < 0 || opts->h < 0) return -7;
+        if (opts->defer < 0 || opts->defer > kTcMaxPanels) return -7;
+        if (defer) *defer = opts->defer;
         for (int r : opts->reserved)
             if (r != 0) return -7;
         if (opts->b > 0) b = opts->b;
@@ -156,52 +159,116 @@ static int factor_args(int m, int n, const void* A, int lda, const int* piv, con
     return 0;
 }
 
-// Schur update with bf16 / fp8 operands on the tensor cores.  L21 and all of
-// U12 are quantized once per step (the first call of the step), then each
-// column range is one tcgen05 launch.
-struct SchurLowp {
-    bool fp8;
-    int n;
-    unsigned char* Lq;
-    unsigned char* Uq;
-    int* expL;
-    int* expU;
-    int* status;
-    mutable int last_k = -1;
-    int operator()(float* A, int lda, int m, int k, int w, int c0, int c1, cudaStream_t s) const {
-        const int r0 = k + w;
-        if (k != last_k) {
-            if (int rc = quantize_l21(A, lda, m, k, w, fp8, Lq, expL, s)) return rc;
-            if (int rc = quantize_u12(A, lda, k, w, r0, n, fp8, Uq, expU, s)) return rc;
-            last_k = k;
-        }
-        const size_t elem = fp8 ? 1 : 2;
-        const int off = c0 - r0;
-        return schur_tc(A + idx(r0, c0, lda), lda, m - r0, c1 - c0, Lq, Uq + static_cast<size_t>(off) * kLowpK * elem,
-                        expL, expU, 0, off, fp8, status, w, s);
-    }
-};
-
-static int factor_lowp(int m, int n, float* A, int lda, int* piv, int* info, int b, int h, int prec,
+// The bf16 / fp8 factorization with deferred trailing updates (the reuse
+// of Section 4.1 and the per-step update cost of Section 7.4 applied to HBM:
+// each pass over the trailing matrix applies up to `defer` panels).  Each
+// step quantizes its L21 and U12 once and adds them to the pending list.
+// Elements receive the pending panels in step order, each as
+// C = fma(-s_p, acc_p, C) with acc_p one panel's fp32 product, so the factors
+// are those of one full trailing update per step, bit for bit:
+//   - after the step's row swaps, the rows of every pending Lq (and their
+//     fp8 exponents) make the same moves, so each row keeps its operands;
+//   - the winners' rows right of the panel (the "row strip") receive the
+//     pending panels before the U12 solve reads them;
+//   - the next panel's columns (the "column strip") receive all pending
+//     panels before the next tournament reads them;
+//   - the rest of the trailing matrix receives them in one pass when
+//     `defer` panels are pending.
+static int factor_lowp(int m, int n, float* A, int lda, int* piv, int* info, int b, int h, int prec, int defer,
                        cudaStream_t s) {
     if (m != n || (b % 128) != 0) return LU_EUNSUPPORTED;
+    LU_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
+    const int kmax = n;
+    if (kmax == 0) return 0;
     const bool fp8 = prec == LU_PREC_FP8;
     const size_t elem = fp8 ? 1 : 2;
-    SchurLowp op{};
-    op.fp8 = fp8;
-    op.n = n;
-    op.status = info;
+    const int d = defer > 0 ? defer : kDeferDefault;
+    struct Slot {
+        unsigned char* Lq = nullptr;
+        unsigned char* Uq = nullptr;
+        int* eLrow = nullptr;
+        int* eU = nullptr;
+    } slot[kTcMaxPanels];
     const size_t nblk = static_cast<size_t>(cdiv(n, 256)) + 1;
-    bool ok = cudaMallocAsync(reinterpret_cast<void**>(&op.Lq), static_cast<size_t>(m) * kLowpK * elem + 256, s) == cudaSuccess &&
-              cudaMallocAsync(reinterpret_cast<void**>(&op.Uq), static_cast<size_t>(n) * kLowpK * elem + 256, s) == cudaSuccess &&
-              cudaMallocAsync(reinterpret_cast<void**>(&op.expL), nblk * sizeof(int), s) == cudaSuccess &&
-              cudaMallocAsync(reinterpret_cast<void**>(&op.expU), nblk * sizeof(int), s) == cudaSuccess;
-    int rc = ok ? factor_loop<float>(m, n, A, lda, piv, info, b, h, op, s) : LU_ENOMEM;
+    bool ok = true;
+    for (int i = 0; i < d && ok; ++i)
+        ok = cudaMallocAsync(reinterpret_cast<void**>(&slot[i].Lq), static_cast<size_t>(m) * kLowpK * elem + 256, s) == cudaSuccess &&
+             cudaMallocAsync(reinterpret_cast<void**>(&slot[i].Uq), static_cast<size_t>(n) * kLowpK * elem + 256, s) == cudaSuccess &&
+             cudaMallocAsync(reinterpret_cast<void**>(&slot[i].eLrow), (static_cast<size_t>(m) + 1) * sizeof(int), s) == cudaSuccess &&
+             cudaMallocAsync(reinterpret_cast<void**>(&slot[i].eU), nblk * sizeof(int), s) == cudaSuccess;
+    FactorWs ws;
+    int rc = ok ? ws_alloc(ws, m, b, h, sizeof(float), s) : LU_ENOMEM;
+    float* a00 = static_cast<float*>(ws.a00);
+    int lo = 0, hi = 0;
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_panel = nullptr, ev_tslu = nullptr, ev_piv = nullptr, ev_u12 = nullptr;
+    if (!rc && (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+                cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, hi) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev_tslu, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev_piv, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev_u12, cudaEventDisableTiming) != cudaSuccess))
+        rc = LU_ELAUNCH;
+    LowpOperand P[kTcMaxPanels];
+    int np = 0;
+    const int* root = nullptr;
+    if (!rc && cudaEventRecord(ev_panel, s) != cudaSuccess) rc = LU_ELAUNCH;
+    if (!rc && cudaStreamWaitEvent(s2, ev_panel, 0) != cudaSuccess) rc = LU_ELAUNCH;
+    if (!rc) rc = tslu_select<float>(A, lda, m, 0, (kmax < b ? kmax : b), h, ws.lists, ws.counts, ws.stride_nodes, a00,
+                                     info, &root, s2);
+    if (!rc && cudaEventRecord(ev_tslu, s2) != cudaSuccess) rc = LU_ELAUNCH;
+    for (int k = 0; k < kmax && rc == 0; k += b) {
+        const int w = (kmax - k) < b ? (kmax - k) : b;
+        const int kn = k + w;
+        const int wn = (kmax - kn) < b ? (kmax - kn) : b;     // next panel width (<= 0: none)
+        if (cudaStreamWaitEvent(s, ev_tslu, 0) != cudaSuccess) { rc = LU_ELAUNCH; break; }
+        rc = pivot_apply<float>(A, lda, m, n, k, w, root, a00, piv, ws.mv, s);
+        if (!rc && np > 0) rc = lowp_row_moves(P, np, fp8, ws.mv, w, s);
+        // the winners' rows right of the panel receive the pending panels
+        if (!rc && np > 0) rc = schur_tc_apply(A, lda, k, kn, w, n - kn, P, np, fp8, info, false, s);
+        if (!rc && cudaEventRecord(ev_piv, s) != cudaSuccess) rc = LU_ELAUNCH;
+        if (!rc && cudaStreamWaitEvent(s2, ev_piv, 0) != cudaSuccess) rc = LU_ELAUNCH;
+        if (!rc) rc = trsm_u12<float>(A, lda, n, k, w, s2);
+        if (!rc && cudaEventRecord(ev_u12, s2) != cudaSuccess) rc = LU_ELAUNCH;
+        if (!rc) rc = trsm_l21<float>(A, lda, m, k, w, A + idx(k, k, lda), lda, s);
+        if (!rc && cudaStreamWaitEvent(s, ev_u12, 0) != cudaSuccess) rc = LU_ELAUNCH;
+        if (rc || kn >= n) break;
+        // this step's operands join the pending list
+        Slot& sl = slot[np];
+        rc = quantize_l21(A, lda, m, k, w, fp8, sl.Lq, sl.eLrow, s);
+        if (!rc) rc = quantize_u12(A, lda, k, w, kn, n, fp8, sl.Uq, sl.eU, s);
+        if (rc) break;
+        P[np++] = LowpOperand{sl.Lq, m - kn, sl.eLrow, sl.Uq, n - kn, sl.eU, kn, kn, w};
+        // the next panel's columns, then its tournament beside the rest
+        rc = schur_tc_apply(A, lda, kn, kn, m - kn, wn, P, np, fp8, info, false, s);
+        if (!rc && cudaEventRecord(ev_panel, s) != cudaSuccess) rc = LU_ELAUNCH;
+        if (!rc && cudaStreamWaitEvent(s2, ev_panel, 0) != cudaSuccess) rc = LU_ELAUNCH;
+        if (!rc) rc = tslu_select<float>(A, lda, m, kn, wn, h, ws.lists, ws.counts, ws.stride_nodes, a00, info,
+                                         &root, s2);
+        if (!rc && cudaEventRecord(ev_tslu, s2) != cudaSuccess) rc = LU_ELAUNCH;
+        if (!rc && np == d) {
+            rc = schur_tc_apply(A, lda, kn, kn + wn, m - kn, n - kn - wn, P, np, fp8, info, true, s);
+            np = 0;
+        }
+    }
+    // join the side stream before the workspace goes back to the pool
+    if (ev_tslu && s2) {
+        cudaEventRecord(ev_tslu, s2);
+        cudaStreamWaitEvent(s, ev_tslu, 0);
+    }
     cudaGetLastError();
-    if (op.Lq) cudaFreeAsync(op.Lq, s);
-    if (op.Uq) cudaFreeAsync(op.Uq, s);
-    if (op.expL) cudaFreeAsync(op.expL, s);
-    if (op.expU) cudaFreeAsync(op.expU, s);
+    ws_free(ws, s);
+    for (int i = 0; i < kTcMaxPanels; ++i) {
+        if (slot[i].Lq) cudaFreeAsync(slot[i].Lq, s);
+        if (slot[i].Uq) cudaFreeAsync(slot[i].Uq, s);
+        if (slot[i].eLrow) cudaFreeAsync(slot[i].eLrow, s);
+        if (slot[i].eU) cudaFreeAsync(slot[i].eU, s);
+    }
+    if (ev_panel) cudaEventDestroy(ev_panel);
+    if (ev_tslu) cudaEventDestroy(ev_tslu);
+    if (ev_piv) cudaEventDestroy(ev_piv);
+    if (ev_u12) cudaEventDestroy(ev_u12);
+    if (s2) cudaStreamDestroy(s2);
     return rc;
 }
 
@@ -227,7 +294,7 @@ extern "C" int lu_gemm_lowp(int M, int N, int K, const float* L, int ldl, const 
     int *eL = nullptr, *eU = nullptr;
     bool ok = cudaMallocAsync(reinterpret_cast<void**>(&Lq), static_cast<size_t>(M) * kLowpK * elem + 256, stream) == cudaSuccess &&
               cudaMallocAsync(reinterpret_cast<void**>(&Uq), static_cast<size_t>(N) * kLowpK * elem + 256, stream) == cudaSuccess &&
-              cudaMallocAsync(reinterpret_cast<void**>(&eL), (static_cast<size_t>(cdiv(M, 256)) + 1) * sizeof(int), stream) == cudaSuccess &&
+              cudaMallocAsync(reinterpret_cast<void**>(&eL), (static_cast<size_t>(M) + 1) * sizeof(int), stream) == cudaSuccess &&
               cudaMallocAsync(reinterpret_cast<void**>(&eU), (static_cast<size_t>(cdiv(N, 256)) + 1) * sizeof(int), stream) == cudaSuccess;
     int rc = LU_ENOMEM;
     if (ok) {
@@ -237,7 +304,8 @@ extern "C" int lu_gemm_lowp(int M, int N, int K, const float* L, int ldl, const 
         // k = 0, r0 = K for L and c0 = K for U.
         rc = quantize_l21(L - static_cast<ptrdiff_t>(K) * ldl, ldl, K + M, 0, K, fp8, Lq, eL, stream);
         if (!rc) rc = quantize_u12(U - K, ldu, 0, K, K, K + N, fp8, Uq, eU, stream);
-        if (!rc) rc = schur_tc(C, ldc, M, N, Lq, Uq, eL, eU, 0, 0, fp8, status, K, stream);
+        const LowpOperand op{Lq, M, eL, Uq, N, eU, 0, 0, K};
+        if (!rc) rc = schur_tc_apply(C, ldc, 0, 0, M, N, &op, 1, fp8, status, false, stream);
     }
     cudaGetLastError();
     if (Lq) cudaFreeAsync(Lq, stream);
@@ -255,12 +323,50 @@ extern "C" int lu_factor_ex(int m, int n, double* A, int lda, int* piv, int* inf
     return factor_loop<double>(m, n, A, lda, piv, info, b, h, SchurF64{}, stream);
 }
 
+extern "C" int lu_factor_host(int m, int n, double* A, int lda, int* piv, int* info, const lu_opts* opts,
+                              cudaStream_t stream) {
+    int b, h, prec;
+    if (int rc = factor_args(m, n, A, lda, piv, info, opts, 8, b, h, prec)) return rc;
+    if (prec != LU_PREC_F64) return LU_EUNSUPPORTED;
+    const int kmax = m < n ? m : n;
+    *info = 0;
+    if (kmax == 0) return 0;
+    const size_t row = static_cast<size_t>(n) * sizeof(double);
+    double* dA = nullptr;
+    int* dpiv = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&dA), row * m, stream) != cudaSuccess ||
+        cudaMallocAsync(reinterpret_cast<void**>(&dpiv), (static_cast<size_t>(kmax) + 1) * sizeof(int), stream) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        if (dA) cudaFreeAsync(dA, stream);
+        return LU_ENOMEM;
+    }
+    int* dinfo = dpiv + kmax;
+    int rc = 0;
+    if (cudaMemcpy2DAsync(dA, row, A, static_cast<size_t>(lda) * sizeof(double), row, m, cudaMemcpyHostToDevice,
+                          stream) != cudaSuccess)
+        rc = LU_ELAUNCH;
+    if (!rc) rc = factor_loop<double>(m, n, dA, n, dpiv, dinfo, b, h, SchurF64{}, stream);
+    if (!rc && (cudaMemcpy2DAsync(A, static_cast<size_t>(lda) * sizeof(double), dA, row, row, m,
+                                  cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+                cudaMemcpyAsync(piv, dpiv, static_cast<size_t>(kmax) * sizeof(int), cudaMemcpyDeviceToHost,
+                                stream) != cudaSuccess ||
+                cudaMemcpyAsync(info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess))
+        rc = LU_ELAUNCH;
+    cudaGetLastError();
+    cudaFreeAsync(dA, stream);
+    cudaFreeAsync(dpiv, stream);
+    if (cudaStreamSynchronize(stream) != cudaSuccess && !rc) rc = LU_ELAUNCH;
+    return rc;
+}
+
 extern "C" int lu_factor_f32(int m, int n, float* A, int lda, int* piv, int* info, const lu_opts* opts,
                              cudaStream_t stream) {
-    int b, h, prec;
-    if (int rc = factor_args(m, n, A, lda, piv, info, opts, 4, b, h, prec)) return rc;
+    int b, h, prec, defer;
+    if (int rc = factor_args(m, n, A, lda, piv, info, opts, 4, b, h, prec, &defer)) return rc;
     if (prec == LU_PREC_F32) return factor_loop<float>(m, n, A, lda, piv, info, b, h, SchurF32{}, stream);
-    if (prec == LU_PREC_BF16 || prec == LU_PREC_FP8) return factor_lowp(m, n, A, lda, piv, info, b, h, prec, stream);
+    if (prec == LU_PREC_BF16 || prec == LU_PREC_FP8)
+        return factor_lowp(m, n, A, lda, piv, info, b, h, prec, defer, stream);
     return -7;
 }
 

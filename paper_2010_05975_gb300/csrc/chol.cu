@@ -133,7 +133,7 @@ static int chol_args(int n, const void* A, int lda, const int* info, const lu_op
     if (info == nullptr) return -4;
     b = (n >= 4096) ? 128 : 64;
     if (opts) {
-        if (opts->b < 0 || opts->h != 0) return -5;
+        if (opts->b < 0 || opts->h != 0 || opts->defer != 0) return -5;
         if (opts->precision != (elem == 8 ? LU_PREC_F64 : LU_PREC_F32) && opts->precision != 0) return -5;
         for (int r : opts->reserved)
             if (r != 0) return -5;

@@ -48,6 +48,30 @@ inline int smem_attr(K* kernel, size_t bytes) {
     return 0;
 }
 
+// Bounded device waits.  Every spin or mbarrier wait of the library gives up
+// after a wall-clock deadline read from %globaltimer (nanoseconds), not
+// after a poll count: a poll may suspend for a hardware-defined time, so a
+// count bounds nothing.  A wait that runs out records an error status that
+// the host turns into LU_ETIMEOUT, and the kernel exits normally.
+constexpr unsigned long long kWaitDefaultNs = 4000000000ull;   // dependency waits: 4 s
+constexpr unsigned long long kDrainWaitNs = 4000000000ull;     // waits for the kernel's own copies in flight
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Per wait site: the deadline of its dependency waits and whether a test has
+// asked it to wait once on something nothing will ever signal (the way the
+// tests make a wait run out without a fault).  Process-wide; set only by
+// lu_test_wait_config.
+struct WaitCfg {
+    unsigned long long wait_ns;
+    int inject;
+};
+WaitCfg wait_cfg(int site);     // site: LU_WAIT_SITE_*
+
 constexpr int kMaxPanel = 256;          // largest supported panel width b
 constexpr int kTsluThreads = 256;       // threads per tournament CTA
 constexpr int kTsluMaxCluster = 8;      // portable cluster size
@@ -143,11 +167,35 @@ void ir_release(IrFactors* f, cudaStream_t s);
 size_t ir_workspace_bytes(int n, int nrhs, int restart);
 
 // Low-precision tensor-core Schur update (csrc/schur_lowp.cu).
-constexpr int kLowpK = 256;     // operand K is padded to this
-size_t lowp_smem_bytes(bool fp8);
-int quantize_l21(const float* A, int lda, int m, int k, int w, bool fp8, void* Lq, int* expL, cudaStream_t s);
+constexpr int kLowpK = 256;     // operand rows are 256 K-elements wide (padded)
+constexpr int kTcMaxPanels = 4; // pending panels one update launch applies
+constexpr int kDeferDefault = 4;   // pending panels of the bf16 / fp8 factorization by default
+// One quantized panel: Lq (rows from the step's first trailing row r0,
+// K-major, kLowpK wide) with per-row fp8 exponents, and UqT (rows = the
+// trailing columns from c0) with one fp8 exponent per 256 rows.
+struct LowpOperand {
+    const void* Lq;
+    int Lrows;
+    const int* eLrow;
+    const void* Uq;
+    int Urows;
+    const int* eU;
+    int r0, c0, w;
+};
+struct LowpMoveArgs {
+    void* Lq[kTcMaxPanels];
+    int* eLrow[kTcMaxPanels];
+    int r0[kTcMaxPanels];
+    int elem, row_bytes;
+};
+size_t lowp_smem_bytes();
+int lowp_kpad(int w, bool fp8);
+int quantize_l21(const float* A, int lda, int m, int k, int w, bool fp8, void* Lq, int* eLrow, cudaStream_t s);
 int quantize_u12(const float* A, int lda, int k, int w, int c0, int c1, bool fp8, void* Uq, int* expU, cudaStream_t s);
-int schur_tc(float* C, int ldc, int M, int N, const void* Lq, const void* Uq, const int* expL, const int* expU,
-             int row_base, int col_base, bool fp8, int* status, int w, cudaStream_t s);
+// A[R0:R0+M, C0:C0+N) -= sum_p s_p q(L_p) q(U_p), panels in order
+int schur_tc_apply(float* A, int lda, int R0, int C0, int M, int N, const LowpOperand* ops, int np, bool fp8,
+                   int* status, bool leave_sms, cudaStream_t s);
+// the step's row moves (pivot_apply's move list) applied to pending Lq rows
+int lowp_row_moves(const LowpOperand* ops, int np, bool fp8, const int* mv, int w, cudaStream_t s);
 
 }  // namespace lu

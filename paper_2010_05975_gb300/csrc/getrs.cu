@@ -133,7 +133,6 @@ __global__ void __launch_bounds__(128) invert_diag_kernel(int n, const T* __rest
 constexpr int kSolveRhs = 64;            // right-hand sides per pass
 constexpr int kSolveTile = 32;           // rows per update tile
 constexpr int kSolveThreads = 256;
-constexpr long long kSolveWaitLimit = 1ll << 24;   // polls of one dependency before giving up
 
 // Item list bookkeeping (device memory, zeroed before each pass).
 struct SolveSync {
@@ -166,16 +165,25 @@ __global__ void solve_offsets_kernel(int n, int* __restrict__ off) {
     off[2 * nblk] = acc;
 }
 
-// Bounded wait by thread 0 until *flag >= want; records a timeout.  After
-// any timeout every wait returns at once, so a broken run ends quickly.
-__device__ __forceinline__ void solve_wait(const int* flag, int want, SolveSync* sy) {
+// Wait by thread 0 until *flag >= want, at most limit_ns of wall-clock time
+// (%globaltimer, read every 64 polls); a wait that runs out records the
+// timeout.  After any timeout every wait returns at once, so a broken run
+// ends quickly (its results are then invalid and the host reports
+// LU_ETIMEOUT).
+__device__ __forceinline__ void solve_wait(const int* flag, int want, SolveSync* sy, unsigned long long limit_ns) {
     const volatile int* f = flag;
     const volatile int* to = &sy->timeout;
-    long long it = 0;
-    while (*f < want) {
-        if (++it > kSolveWaitLimit || ((it & 255) == 0 && *to)) {
-            atomicExch(&sy->timeout, 1);
-            return;
+    unsigned long long t0 = 0;
+    for (unsigned it = 1; *f < want; ++it) {
+        if ((it & 63) == 0) {
+            if (*to) return;
+            const unsigned long long now = global_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > limit_ns) {
+                atomicExch(&sy->timeout, 1);
+                return;
+            }
         }
         __nanosleep(32);
     }
@@ -189,7 +197,8 @@ __global__ void __launch_bounds__(kSolveThreads) solve_items_kernel(int n, const
                                                                     const T* __restrict__ DT,
                                                                     const int* __restrict__ off, T* Y, T* X,
                                                                     int* fdone, int* bdone, int* xpf, int* xpb,
-                                                                    SolveSync* sy, int chol) {
+                                                                    SolveSync* sy, int chol,
+                                                                    unsigned long long wait_ns, int inject) {
     constexpr int NB = SolveNB<T>::value;
     constexpr int TR = kSolveTile;
     constexpr int TPB = NB / TR;                     // tiles (and solve parts) per block
@@ -247,18 +256,20 @@ __global__ void __launch_bounds__(kSolveThreads) solve_items_kernel(int n, const
         }
         // 2. dependencies, all on earlier items
         if (tid == 0) {
+            // test hook: the first item also waits on a counter nothing increments
+            if (inject && s_item == 0) solve_wait(&sy->pad[0], 1, sy, wait_ns);
             if (part) {
                 const int kb = ph == 0 ? b : nblk - 1 - b;
                 for (int u = b * TPB; u < min(ntile, (b + 1) * TPB); ++u)
-                    solve_wait(ph == 0 ? fdone + u : bdone + u, kb, sy);
-                if (ph == 1) solve_wait(xpf + b, parts, sy);
+                    solve_wait(ph == 0 ? fdone + u : bdone + u, kb, sy, wait_ns);
+                if (ph == 1) solve_wait(xpf + b, parts, sy, wait_ns);
             } else {
-                solve_wait(ph == 0 ? xpf + b : xpb + b, parts, sy);
+                solve_wait(ph == 0 ? xpf + b : xpb + b, parts, sy, wait_ns);
                 if (ph == 1) {
                     const int tb = t / TPB;
-                    solve_wait(xpf + tb, cdiv(min(NB, n - tb * NB), TR), sy);
+                    solve_wait(xpf + tb, cdiv(min(NB, n - tb * NB), TR), sy, wait_ns);
                 }
-                solve_wait(ph == 0 ? fdone + t : bdone + t, ph == 0 ? b : nblk - 1 - b, sy);
+                solve_wait(ph == 0 ? fdone + t : bdone + t, ph == 0 ? b : nblk - 1 - b, sy, wait_ns);
             }
             __threadfence();
         }
@@ -331,8 +342,9 @@ static int solve_launch(int n, const SolvePlan<T>& p, T* Y, T* X, int* fdone, in
                         SolveSync* sy, cudaStream_t s) {
     const int G = solve_grid<T, NCW>();
     if (G <= 0) return LU_EUNSUPPORTED;
-    solve_items_kernel<T, NCW><<<G, kSolveThreads, solve_smem<T, NCW>(), s>>>(n, p.LU, p.lda, p.DT, p.off, Y, X,
-                                                                              fdone, bdone, xpf, xpb, sy, p.chol);
+    const WaitCfg wc = wait_cfg(LU_WAIT_SITE_SOLVE);
+    solve_items_kernel<T, NCW><<<G, kSolveThreads, solve_smem<T, NCW>(), s>>>(
+        n, p.LU, p.lda, p.DT, p.off, Y, X, fdone, bdone, xpf, xpb, sy, p.chol, wc.wait_ns, wc.inject);
     count_launches(1);
     return 0;
 }

@@ -765,8 +765,6 @@ extern "C" int ir_solve(int n, int nrhs, const double* A, int lda, const double*
 // allocator.  Its reduction scratch is a fixed array in this file instead of
 // a cudaMallocAsync buffer, which bounds nrhs.
 // ---------------------------------------------------------------------------
-#include <mutex>
-
 namespace lu {
 
 constexpr int kNoAllocMaxRhs = 64;
@@ -779,30 +777,18 @@ constexpr size_t kNoAllocWords =
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocWords];
 
 namespace {
-std::mutex g_noalloc_mu;
-constexpr int kNoAllocMaxDevices = 64;
-double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
-
 // Device address of this device's scratch array.  In host code the array's
 // name is only a host-side stand-in, so the address comes from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress with the device current.  It is looked up on every
+// call (a cheap host-side query): an address kept from an earlier call would
+// point into a destroyed context after cudaDeviceReset.
 int noalloc_scratch(double** out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
         cudaGetLastError();
         return LU_ELAUNCH;
     }
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return LU_EUNSUPPORTED;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (g_noalloc_ptr[dev] == nullptr) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
-            cudaGetLastError();
-            return LU_ELAUNCH;
-        }
-        g_noalloc_ptr[dev] = static_cast<double*>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = static_cast<double*>(p);
     return 0;
 }
 }  // namespace

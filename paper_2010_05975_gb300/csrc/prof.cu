@@ -107,3 +107,36 @@ extern "C" int lu_prof_end(lu_prof_entry* out, int max_entries, int* n_entries) 
 }
 
 extern "C" unsigned long long lu_kernel_launch_count(void) { return g_launches.load(); }
+
+// ---------------------------------------------------------------------------
+// Wait deadlines and the test hook that makes a wait run out
+// ---------------------------------------------------------------------------
+namespace lu {
+namespace {
+std::atomic<unsigned long long> g_wait_ns[LU_WAIT_NSITES] = {};
+std::atomic<int> g_inject[LU_WAIT_NSITES] = {};
+}  // namespace
+
+WaitCfg wait_cfg(int site) {
+    WaitCfg c{kWaitDefaultNs, 0};
+    if (site < 0 || site >= LU_WAIT_NSITES) return c;
+    const unsigned long long ns = g_wait_ns[site].load();
+    if (ns > 0) c.wait_ns = ns;
+    c.inject = g_inject[site].load();
+    return c;
+}
+}  // namespace lu
+
+extern "C" int lu_test_wait_config(int site, long long wait_ns, int inject) {
+    if (site < 0 || site >= LU_WAIT_NSITES) return -1;
+    if (wait_ns < 0 || wait_ns > 600000000000ll) return -2;
+    if (inject != 0 && inject != 1) return -3;
+    g_wait_ns[site].store(static_cast<unsigned long long>(wait_ns));
+    g_inject[site].store(inject);
+    return 0;
+}
+
+extern "C" long long lu_wait_deadline_ns(int site) {
+    if (site < 0 || site >= LU_WAIT_NSITES) return -1;
+    return static_cast<long long>(wait_cfg(site).wait_ns);
+}

@@ -17,7 +17,7 @@ def declared_functions():
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
-        for m in re.finditer(r"^\s*(?:int|void|size_t|double|unsigned long long|const char\s*\*)\s+\**(\w+)\s*\(", src, flags=re.M):
+        for m in re.finditer(r"^\s*(?:int|void|size_t|double|unsigned long long|long long|const char\s*\*)\s+\**(\w+)\s*\(", src, flags=re.M):
             names.add(m.group(1))
     return sorted(names)
 
@@ -108,3 +108,45 @@ def test_python_cholesky_refuses_bad_tensors(native):
         native.chol_solve(torch.zeros(4, 4, dtype=torch.float16), torch.zeros(4))
     with pytest.raises(TypeError):
         native.chol_solve(torch.zeros(4, 4, dtype=torch.float64), torch.zeros(4, dtype=torch.float64))
+
+
+def test_host_factor_argument_errors(native):
+    """lu_factor_host checks its host arguments before it allocates or copies."""
+    lib = native.library()
+    s = ctypes.c_void_p(0)
+    dummy = ctypes.c_void_p(16)
+    assert lib.lu_factor_host(-1, 4, dummy, 4, dummy, dummy, None, s) == -1
+    assert lib.lu_factor_host(4, -1, dummy, 4, dummy, dummy, None, s) == -2
+    assert lib.lu_factor_host(4, 4, None, 4, dummy, dummy, None, s) == -3
+    assert lib.lu_factor_host(4, 4, dummy, 3, dummy, dummy, None, s) == -4
+    assert lib.lu_factor_host(4, 4, dummy, 4, None, dummy, None, s) == -5
+    assert lib.lu_factor_host(4, 4, dummy, 4, dummy, None, None, s) == -6
+    bf16 = native._native.lu_opts(32, 128, native.LU_PREC_BF16)
+    info = ctypes.c_int(7)
+    assert lib.lu_factor_host(4, 4, dummy, 4, dummy, ctypes.byref(info), ctypes.byref(bf16), s) == \
+        native.LU_EUNSUPPORTED
+    # an empty matrix needs no device: info is set, nothing else happens
+    assert lib.lu_factor_host(0, 0, None, 1, None, ctypes.byref(info), None, s) == 0
+    assert info.value == 0
+
+
+def test_wait_deadline_config_host_side(native):
+    """The wait-deadline hook: argument checks, the 4 s default, a set value
+    and its reset (host-side state only; no device work)."""
+    lib = native.library()
+    TC, SOLVE = native.LU_WAIT_SITE_TC, native.LU_WAIT_SITE_SOLVE
+    assert lib.lu_test_wait_config(2, 0, 0) == -1
+    assert lib.lu_test_wait_config(-1, 0, 0) == -1
+    assert lib.lu_test_wait_config(TC, -5, 0) == -2
+    assert lib.lu_test_wait_config(TC, 601 * 10 ** 9, 0) == -2
+    assert lib.lu_test_wait_config(TC, 0, 2) == -3
+    assert lib.lu_wait_deadline_ns(3) == -1
+    assert lib.lu_wait_deadline_ns(TC) == 4 * 10 ** 9
+    assert lib.lu_wait_deadline_ns(SOLVE) == 4 * 10 ** 9
+    try:
+        assert lib.lu_test_wait_config(SOLVE, 12345, 1) == 0
+        assert lib.lu_wait_deadline_ns(SOLVE) == 12345
+        assert lib.lu_wait_deadline_ns(TC) == 4 * 10 ** 9      # sites are independent
+    finally:
+        assert lib.lu_test_wait_config(SOLVE, 0, 0) == 0
+    assert lib.lu_wait_deadline_ns(SOLVE) == 4 * 10 ** 9

@@ -20,14 +20,14 @@ def native():
     return g, nat, L
 
 
-def gpu_factor_f32(A32, b, h, prec=1):
+def gpu_factor_f32(A32, b, h, prec=1, defer=0):
     torch = cuda_or_fail()
     g, nat, L = native()
     dA = torch.from_numpy(A32.copy()).cuda()
     m, n = A32.shape
     piv = torch.zeros(max(min(m, n), 1), dtype=torch.int32, device="cuda")
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
-    opts = nat.lu_opts(b, h, prec)
+    opts = nat.lu_opts(b, h, prec, defer)
     rc = L.lu_factor_f32(m, n, dA.data_ptr(), n, piv.data_ptr(), info.data_ptr(), ctypes.byref(opts),
                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == 0, rc
@@ -188,3 +188,34 @@ def test_lowp_factor_rounded_first_update_bitwise(oracle_mod, prec, b):
     np.testing.assert_array_equal(LUg, LU)
     LUo, po, io = oracle_mod.lu_factor_f32(A, b=b, h=128, lowp=prec - 1)
     np.testing.assert_array_equal(LUg, LUo)
+
+
+# --- deferred trailing updates: the same factors for every deferral ---------
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("n,b", [(1100, 128), (2048, 128), (1500, 256), (777, 128)])
+def test_lowp_deferred_updates_bitwise(prec, n, b):
+    """Holding back up to 4 panels' updates and applying them in one pass
+    (each panel into its own accumulator, applied in step order) must give
+    the per-step factors bit for bit, on generic inputs where every rounding
+    counts.  n = 777 has rows that are not 16-byte aligned (the epilogue's
+    per-thread path); the others use the TMA epilogue."""
+    A = wl.matrix_uniform(n, n, seed=n + 11 * prec, stream=50).astype(np.float32)
+    ref, pref, iref = gpu_factor_f32(A, b, 128, prec=prec, defer=1)
+    assert iref == 0
+    for d in (2, 3, 4):
+        LUg, pg, ig = gpu_factor_f32(A, b, 128, prec=prec, defer=d)
+        assert ig == 0
+        np.testing.assert_array_equal(pg, pref)
+        np.testing.assert_array_equal(LUg, ref)
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+def test_lowp_closed_form_every_deferral(oracle_mod, prec):
+    """The exact closed form comes back bit for bit at every deferral."""
+    A, LU = cf.exact_factors(1100)
+    for d in (1, 2, 3, 4):
+        LUg, pg, ig = gpu_factor_f32(A, 128, 128, prec=prec, defer=d)
+        assert ig == 0
+        np.testing.assert_array_equal(pg, np.arange(1100))
+        np.testing.assert_array_equal(LUg, LU)

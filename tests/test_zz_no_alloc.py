@@ -1,7 +1,13 @@
 """lu_residual_noalloc: the residual and backward error for callers that
-cannot allocate device memory while they run (its scratch is a fixed array
-inside the library).  Checked through the C ABI against lu_residual on two
-calls in a row, so that a second call does not read the first one's leftovers.
+cannot allocate device memory while they run -- a serving loop that reserves
+all of its memory before it takes requests, or a process whose GPU memory
+another framework's caching allocator owns.  Its scratch is a fixed array
+inside the library.
+
+Checked through the C ABI on two calls in a row (so that a second call does
+not read the first one's leftovers): against the host's binary64 B - AX, the
+oracle's backward error and the allocating entry point lu_residual; and the
+calls must leave the device's stream-ordered pool and free memory untouched.
 This file is collected last on purpose."""
 import ctypes
 
@@ -12,6 +18,10 @@ import workloads as wl
 from tests.gpu_util import cuda_or_fail, lib
 
 pytestmark = pytest.mark.gpu
+
+# CUmemPool_attribute values (cuda.h)
+_USED_MEM_CURRENT = 7
+_USED_MEM_HIGH = 8
 
 
 def _entry():
@@ -26,31 +36,96 @@ def _entry():
     return L
 
 
+class DefaultPool:
+    """Read-only view of the current device's default stream-ordered memory
+    pool through the driver API (the pool cudaMallocAsync draws from)."""
+
+    def __init__(self, torch):
+        self.cu = ctypes.CDLL("libcuda.so.1")
+        dev = ctypes.c_int(0)
+        assert self.cu.cuDeviceGet(ctypes.byref(dev), torch.cuda.current_device()) == 0
+        self.pool = ctypes.c_void_p(0)
+        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+
+    def get(self, attr):
+        v = ctypes.c_uint64(0)
+        assert self.cu.cuMemPoolGetAttribute(self.pool, attr, ctypes.byref(v)) == 0
+        return v.value
+
+    def reset_high(self):
+        zero = ctypes.c_uint64(0)
+        assert self.cu.cuMemPoolSetAttribute(self.pool, _USED_MEM_HIGH, ctypes.byref(zero)) == 0
+
+
 def _call(fn, A, X, B, torch):
     n, nr = X.shape
     R = torch.full((n, nr), float("nan"), dtype=torch.float64, device="cuda")
     eta = torch.full((nr,), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
     rc = fn(n, nr, A.data_ptr(), n, X.data_ptr(), nr, B.data_ptr(), nr, R.data_ptr(), nr, eta.data_ptr(),
             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     torch.cuda.synchronize()
     return rc, R.cpu().numpy(), eta.cpu().numpy()
 
 
-def test_noalloc_matches_allocating_entry_point_twice():
+def test_noalloc_matches_host_residual_and_oracle_twice(oracle_mod):
     torch = cuda_or_fail()
     L = _entry()
-    cases = [(700, 16, 1), (1500, 5, 2)]          # two calls in a row, different shapes
+    cases = [(700, 16, 1), (1500, 5, 2), (300, 64, 3)]      # calls in a row, different shapes
     for n, nr, seed in cases:
-        A = torch.from_numpy(wl.matrix_uniform(n, n, seed=seed)).cuda()
-        X = torch.from_numpy(wl.matrix_normal(n, nr, seed=seed + 10)).cuda()
-        B = torch.from_numpy(wl.matrix_normal(n, nr, seed=seed + 20)).cuda()
-        rc0, R0, e0 = _call(L.lu_residual, A, X, B, torch)
+        An = wl.matrix_uniform(n, n, seed=seed)
+        Xn = wl.matrix_normal(n, nr, seed=seed + 10)
+        Bn = wl.matrix_normal(n, nr, seed=seed + 20)
+        A, X, B = (torch.from_numpy(M).cuda() for M in (An, Xn, Bn))
         rc1, R1, e1 = _call(L.lu_residual_noalloc, A, X, B, torch)
-        assert rc0 == 0 and rc1 == 0
-        scale = np.abs(A.cpu().numpy()).sum(axis=1).max() * np.abs(X.cpu().numpy()).max()
-        assert np.abs(R1 - R0).max() <= 4 * n * 2.0 ** -53 * scale
+        assert rc1 == 0
+        # the host's binary64 residual: |R - (B - AX)| within n roundings of |A||X| + |B|
+        Rh = Bn - An @ Xn
+        bound = 4 * n * 2.0 ** -53 * (np.abs(An) @ np.abs(Xn) + np.abs(Bn))
+        assert (np.abs(R1 - Rh) <= bound).all()
+        # the oracle's normwise backward error, column by column
+        eo = oracle_mod.backward_error(An, Bn, Xn)
+        np.testing.assert_allclose(e1, eo, rtol=1e-10, atol=0)
+        # and the allocating entry point
+        rc0, R0, e0 = _call(L.lu_residual, A, X, B, torch)
+        assert rc0 == 0
+        assert (np.abs(R1 - R0) <= bound).all()
         np.testing.assert_allclose(e1, e0, rtol=1e-12)
-        assert np.isfinite(e1).all()
+
+
+def test_noalloc_allocates_nothing():
+    """Around a call (after a first one, which may load the library's device
+    code), the default pool's used-memory high watermark stays where it was
+    and the device's free memory does not change; the same measurement around
+    lu_residual does see its workspace allocation."""
+    torch = cuda_or_fail()
+    L = _entry()
+    pool = DefaultPool(torch)
+    n, nr = 1000, 12
+    A = torch.from_numpy(wl.matrix_uniform(n, n, seed=7)).cuda()
+    X = torch.from_numpy(wl.matrix_normal(n, nr, seed=8)).cuda()
+    B = torch.from_numpy(wl.matrix_normal(n, nr, seed=9)).cuda()
+    assert _call(L.lu_residual_noalloc, A, X, B, torch)[0] == 0
+    R = torch.empty((n, nr), dtype=torch.float64, device="cuda")
+    eta = torch.empty(nr, dtype=torch.float64, device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def measured(fn):
+        torch.cuda.synchronize()
+        pool.reset_high()
+        used0 = pool.get(_USED_MEM_CURRENT)
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(2):
+            assert fn(n, nr, A.data_ptr(), n, X.data_ptr(), nr, B.data_ptr(), nr, R.data_ptr(), nr,
+                      eta.data_ptr(), s) == 0
+        torch.cuda.synchronize()
+        return used0, pool.get(_USED_MEM_HIGH), free0, torch.cuda.mem_get_info()[0]
+
+    used0, high, free0, free1 = measured(L.lu_residual_noalloc)
+    assert high == used0
+    assert free1 == free0
+    used0, high, _, _ = measured(L.lu_residual)
+    assert high > used0                      # the check sees a stream-ordered allocation
 
 
 def test_noalloc_rejects_too_many_rhs():
