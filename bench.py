@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--lowp-k", type=int, default=256, help="K of the lowp_gemm workload")
     ap.add_argument("--lowp-prec", default="bf16,fp8", help="operand formats of the lowp_gemm / lowp_factor workloads")
     ap.add_argument("--defers", default="1,2,4", help="deferrals measured by the lowp_factor workload")
+    ap.add_argument("--lowp-b", type=int, default=128, help="panel width of the lowp_factor workload")
+    ap.add_argument("--serve-s", type=float, default=10.0, help="arrival window of the serving workload (s)")
+    ap.add_argument("--serve-slots", type=int, default=16, help="slot workers of the serving workload")
     ap.add_argument("--mixed-n", type=int, default=32768)
     ap.add_argument("--chol-n", type=int, default=32768, help="order of the Cholesky measurement")
     ap.add_argument("--chol-dtypes", default="f64,f32", help="Cholesky arithmetic(s) to measure")
@@ -415,67 +418,94 @@ def run_cholesky(a, dev, b=128, warmup=1, steps=2, nrhs=16):
 # serving: Poisson arrivals, n log-uniform [32, 8192], 1-64 rhs,
 # kappa log-uniform [1e1, 1e6], 20% repeat matrix ids, 120 GB budget
 # ---------------------------------------------------------------------------
-def run_serving(a, dev, rate=2000.0, count=400, pool=24, slots=6, budget=120 << 30):
+def run_serving(a, dev, rate=2000.0, duration=None, pool=24, slots=None, budget=120 << 30, max_queue=4000):
+    """Fixed-duration Poisson run: requests arrive at `rate` for `duration`
+    seconds; the server admits by HBM budget, batches small requests into
+    shared launches and runs large ones on slots; a full queue sheds load
+    (LU_EBUSY, counted as rejected).  Reports offered and achieved rates,
+    latency and service-time percentiles and the batched share."""
     import time
     import torch
     import paper_2010_05975_gb300 as g
     import workloads as wl
+    duration = a.serve_s if duration is None else duration
+    slots = a.serve_slots if slots is None else slots
     sizes = wl.batch_sizes(pool, 32, 8192, seed=a.seed, stream=31)
     ku = wl.uniform01(a.seed, 33, np.arange(pool, dtype=np.uint64))
     kappas = 10.0 ** (1.0 + 5.0 * ku)
     mats = [householder_on_device(int(n), float(k), 500 + i, dev) for i, (n, k) in enumerate(zip(sizes, kappas))]
+    arrivals = wl.poisson_arrivals(rate, duration, seed=a.seed)
+    count = len(arrivals)
     u = wl.uniform01(a.seed, 35, np.arange(3 * count, dtype=np.uint64)).reshape(3, count)
     midx = np.minimum(np.floor(u[0] * pool).astype(int), pool - 1)
     nrhs = 1 + np.minimum(np.floor(u[1] * 64).astype(int), 63)
     repeat = u[2] < 0.2
-    arrivals = wl.poisson_arrivals(rate, 4.0 * count / rate + 1.0, seed=a.seed)[:count]
     gen = torch.Generator(device=dev)
     gen.manual_seed(a.seed)
-    Bs = [torch.randn(mats[m].shape[0], int(r), dtype=torch.float64, device=dev, generator=gen)
-          for m, r in zip(midx, nrhs)]
+    Bpool = [torch.randn(int(n), 64, dtype=torch.float64, device=dev, generator=gen) for n in sizes]
     torch.cuda.synchronize(dev)
-    out = {"requests": count, "offered_rate": rate, "pool_matrices": pool, "slots": slots,
-           "budget_bytes": budget, "n_range": [32, 8192], "nrhs_range": [1, 64], "kappa_range": [1e1, 1e6],
-           "repeat_fraction": float(repeat.mean())}
-    with g.Server(budget, max_slots=slots) as srv:
-        # warm-up: one request per precision path, not timed
-        wt = [srv.enqueue(mats[i], Bs[0][: mats[i].shape[0]] if Bs[0].shape[0] == mats[i].shape[0] else
-                          torch.ones(mats[i].shape[0], 1, dtype=torch.float64, device=dev), borrow=True)
-              for i in range(min(3, pool))]
+    out = {"duration_s": duration, "offered_rate": rate, "requests_offered": count, "pool_matrices": pool,
+           "slots": slots, "budget_bytes": budget, "max_queue": max_queue, "n_range": [32, 8192],
+           "nrhs_range": [1, 64], "kappa_range": [1e1, 1e6], "repeat_fraction": float(repeat.mean()),
+           "small_n_max": 1024}
+    with g.Server(budget, max_slots=slots, max_queue=max_queue) as srv:
+        # warm-up: one request of each path, not timed
+        wt = [srv.enqueue(mats[i], Bpool[i][:, :2], borrow=True) for i in range(min(4, pool))]
         srv.wait(wt)
         t0 = time.perf_counter()
-        pending, res, t_last = {}, {}, t0
+        pending, res, rejected = {}, {}, 0
         for i in range(count):
             while time.perf_counter() - t0 < arrivals[i]:
                 time.sleep(0.0002)
-            mid = int(midx[i]) + 1 if repeat[i] else 0
-            pending[srv.enqueue(mats[midx[i]], Bs[i], matrix_id=mid, borrow=True)] = i
+            m = int(midx[i])
+            mid = m + 1 if repeat[i] else 0
+            try:
+                t = srv.enqueue(mats[m], Bpool[m][:, : int(nrhs[i])], matrix_id=mid, borrow=True)
+                pending[t] = i
+            except g.LuError as e:
+                if e.code != g.LU_EBUSY:
+                    raise
+                rejected += 1
             for t in list(pending)[:8]:
                 r = srv.poll(t)
                 if r["status"] in ("done", "failed"):
-                    res[pending.pop(t)] = r
-                    t_last = time.perf_counter()
+                    res[pending.pop(t)] = (r, time.perf_counter())
+        t_arr = time.perf_counter() - t0
         while pending:
             for t in list(pending):
                 r = srv.poll(t)
                 if r["status"] in ("done", "failed"):
-                    res[pending.pop(t)] = r
-                    t_last = time.perf_counter()
+                    res[pending.pop(t)] = (r, time.perf_counter())
             time.sleep(0.0005)
+        t_end = time.perf_counter() - t0
         st = srv.stats()
-    lat = np.array([r["latency_s"] for r in res.values()])
-    svc = np.array([r["latency_s"] - r["queue_s"] for r in res.values()])
-    ok = [r for r in res.values() if r["status"] == "done"]
-    out.update({"completed": len(ok), "failed": count - len(ok),
-                "solves_per_s": len(ok) / (t_last - t0), "wall_s": t_last - t0,
-                "p50_latency_ms": 1e3 * float(np.percentile(lat, 50)),
-                "p99_latency_ms": 1e3 * float(np.percentile(lat, 99)),
-                "p50_service_ms": 1e3 * float(np.percentile(svc, 50)),
-                "p99_service_ms": 1e3 * float(np.percentile(svc, 99)),
-                "max_eta": float(max(r["eta"] for r in ok)) if ok else None,
-                "cache_hits": int(sum(r["cache_hit"] for r in ok)),
+    ok = [(i, r) for i, (r, _) in res.items() if r["status"] == "done"]
+    lat = np.array([r["latency_s"] for _, r in ok]) if ok else np.zeros(1)
+    svc = np.array([r["latency_s"] - r["queue_s"] for _, r in ok]) if ok else np.zeros(1)
+    nsm = np.array([int(sizes[midx[i]]) for i, _ in ok]) if ok else np.zeros(1)
+    small = nsm <= 1024
+    bat = np.array([r["batched"] for _, r in ok]) if ok else np.zeros(1)
+
+    def pct(x, q):
+        return 1e3 * float(np.percentile(x, q)) if len(x) else None
+    out.update({"completed": len(ok), "failed": len(res) - len(ok), "rejected": rejected,
+                "arrival_window_s": t_arr, "wall_s": t_end,
+                "achieved_rate": len(ok) / t_end, "solves_per_s": len(ok) / t_end,
+                "p50_latency_ms": pct(lat, 50), "p99_latency_ms": pct(lat, 99),
+                "p50_service_ms": pct(svc, 50), "p99_service_ms": pct(svc, 99),
+                "small": {"completed": int(small.sum()), "p50_latency_ms": pct(lat[small], 50),
+                          "p99_latency_ms": pct(lat[small], 99), "batched_share": float(bat[small].mean())
+                          if small.any() else None},
+                "large": {"completed": int((~small).sum()), "p50_latency_ms": pct(lat[~small], 50),
+                          "p99_latency_ms": pct(lat[~small], 99), "p50_service_ms": pct(svc[~small], 50),
+                          "p99_service_ms": pct(svc[~small], 99)},
+                "small_service_ms": {"p50": pct(svc[small], 50), "p99": pct(svc[small], 99)},
+                "batches": int(st["batches"]), "batched": int(st["batched"]),
+                "mean_batch": float(st["batched"]) / max(1, int(st["batches"])),
+                "max_eta": float(max(r["eta"] for _, r in ok)) if ok else None,
+                "cache_hits": int(sum(r["cache_hit"] for _, r in ok)),
                 "peak_bytes": int(st["peak_bytes"]), "peak_running": int(st["peak_running"])})
-    del mats, Bs
+    del mats, Bpool
     torch.cuda.empty_cache()
     return out
 
@@ -516,7 +546,7 @@ def run_lowp_factor(a, dev, warmup=1):
     torch.cuda.empty_cache()
     A = torch.empty_like(A0)
     stream = torch.cuda.current_stream(dev)
-    out = {"n": n, "b": 128, "h": 128, "cases": []}
+    out = {"n": n, "b": a.lowp_b, "h": 128, "cases": []}
     for name in a.lowp_prec.split(","):
         prec = {"bf16": g.LU_PREC_BF16, "fp8": g.LU_PREC_FP8}[name]
         for d in [int(x) for x in a.defers.split(",")]:
@@ -530,7 +560,7 @@ def run_lowp_factor(a, dev, warmup=1):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                piv, info = g.lu_factor_f32(A, b=128, h=128, precision=prec, stream=stream, defer=d)
+                piv, info = g.lu_factor_f32(A, b=a.lowp_b, h=128, precision=prec, stream=stream, defer=d)
                 e1.record(stream)
                 torch.cuda.synchronize(dev)
                 if prof:

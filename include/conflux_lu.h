@@ -348,11 +348,16 @@ typedef struct {
     int max_slots;              /* requests in flight at once (default 4)      */
     int precision;              /* default factorization precision (BF16)      */
     double tol;                 /* default backward-error target (1e-12)       */
-    int max_queue;              /* pending requests allowed (0: unlimited)     */
+    int max_queue;              /* pending requests allowed per path (slots,
+                                   shared batches; 0: unlimited)                */
     int dry_run;                /* 1: scheduler test mode, no device work: each
                                    request holds its budget for a time
                                    proportional to n^3 and computes nothing    */
-    int reserved[4];
+    int batch_n_max;            /* requests with n up to this share batched
+                                   launches (binary32 factors, binary64
+                                   refinement); 0: 1024, -1: none; <= 1024     */
+    int batch_max;              /* most requests in one shared batch (0: 256)  */
+    int reserved[2];            /* must be zero                                 */
 } serve_cfg;
 
 typedef struct {
@@ -379,6 +384,7 @@ typedef struct {
     double queue_s;             /* enqueue -> start                              */
     int iters, gmres_iters, path, precision;   /* as ir_result                  */
     int cache_hit;              /* factors came from the cache                   */
+    int batched;                /* solved in a shared batched launch             */
 } serve_status;
 
 typedef struct {
@@ -386,6 +392,8 @@ typedef struct {
     int queued, running, peak_running;
     long long completed, failed, cache_hits, evictions;
     int cache_entries;
+    long long batches;          /* shared batched launches run                   */
+    long long batched;          /* requests solved in them                       */
 } serve_stats;
 
 /* Create a server (its worker threads and streams) on the current device.

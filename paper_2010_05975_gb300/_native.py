@@ -52,7 +52,7 @@ class ir_result(ctypes.Structure):
 class serve_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("precision", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_queue", ctypes.c_int), ("dry_run", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("batch_n_max", ctypes.c_int), ("batch_max", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class serve_req(ctypes.Structure):
@@ -66,14 +66,15 @@ class serve_status(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("error", ctypes.c_int), ("eta", ctypes.c_double),
                 ("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double), ("iters", ctypes.c_int),
                 ("gmres_iters", ctypes.c_int), ("path", ctypes.c_int), ("precision", ctypes.c_int),
-                ("cache_hit", ctypes.c_int)]
+                ("cache_hit", ctypes.c_int), ("batched", ctypes.c_int)]
 
 
 class serve_stats(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
                 ("queued", ctypes.c_int), ("running", ctypes.c_int), ("peak_running", ctypes.c_int),
                 ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong), ("cache_hits", ctypes.c_longlong),
-                ("evictions", ctypes.c_longlong), ("cache_entries", ctypes.c_int)]
+                ("evictions", ctypes.c_longlong), ("cache_entries", ctypes.c_int),
+                ("batches", ctypes.c_longlong), ("batched", ctypes.c_longlong)]
 
 
 SERVE_PENDING, SERVE_RUNNING, SERVE_DONE, SERVE_FAILED = 0, 1, 2, 3

@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 #include <utility>
+#include <vector>
 
 #define LU_TRY(expr)                                                  \
     do {                                                              \
@@ -165,6 +166,25 @@ int ir_refine(IrFactors* f, const double* A, int lda, int nrhs, const double* B,
               const ir_opts* o, ir_result* res, cudaStream_t s);
 void ir_release(IrFactors* f, cudaStream_t s);
 size_t ir_workspace_bytes(int n, int nrhs, int restart);
+
+// One request of a shared (batched) solve launch (csrc/serve_batch.cu).
+// Device pointers; n <= 1024, 1 <= nrhs <= 64.
+struct BatchReq {
+    const double* A;           // binary64 matrix (lda)
+    const double* B;           // right-hand sides (ldb)
+    double* X;                 // solution, n x nrhs (ld nrhs)
+    double* R;                 // residual, n x nrhs (ld nrhs)
+    float* r;                  // binary32 correction, n x nrhs (ld nrhs)
+    float* F;                  // binary32 factors, n x n (ld n)
+    int* piv;                  // their pivots
+    double* cw;                // 2 * nrhs scratch: max|b_c|, then max|r_c|
+    double anorm;              // ||A||_inf (set by the launch)
+    int lda, ldb, n, nrhs;
+    int factor;                // 1: F is copied from A and factored here; 0: F holds cached factors
+    int pad;
+};
+int batch_solve(std::vector<BatchReq>& reqs, const std::vector<double>& tol, int max_iter, std::vector<int>& out,
+                std::vector<int>& iters, std::vector<double>& eta, cudaStream_t s);
 
 // Low-precision tensor-core Schur update (csrc/schur_lowp.cu).
 constexpr int kLowpK = 256;     // operand rows are 256 K-elements wide (padded)

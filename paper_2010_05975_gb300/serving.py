@@ -15,10 +15,13 @@ class Server:
     """Continuous-batching linear-solve server on the current CUDA device."""
 
     def __init__(self, hbm_budget_bytes: int, max_slots: int = 4, precision: int = 0, tol: float = 0.0,
-                 max_queue: int = 0, dry_run: bool = False):
+                 max_queue: int = 0, dry_run: bool = False, batch_n_max: int = 0, batch_max: int = 0):
+        """batch_n_max: requests with n up to this share batched launches
+        (0: 1024, -1: every request takes a slot of its own); batch_max:
+        most requests per shared batch (0: 256)."""
         self._lib = nat.library()
         cfg = nat.serve_cfg(int(hbm_budget_bytes), int(max_slots), int(precision), float(tol), int(max_queue),
-                            1 if dry_run else 0)
+                            1 if dry_run else 0, int(batch_n_max), int(batch_max))
         h = ctypes.c_void_p()
         nat.check("serve_create", self._lib.serve_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
@@ -65,7 +68,7 @@ class Server:
         nat.check("serve_poll", rc)
         out = {"status": STATUS[st.status], "error": st.error, "eta": st.eta, "latency_s": st.latency_s,
                "queue_s": st.queue_s, "iters": st.iters, "gmres_iters": st.gmres_iters, "path": st.path,
-               "precision": st.precision, "cache_hit": st.cache_hit}
+               "precision": st.precision, "cache_hit": st.cache_hit, "batched": st.batched}
         if st.status in (nat.SERVE_DONE, nat.SERVE_FAILED):
             self._shapes.pop(ticket, None)
             self._borrowed.pop(ticket, None)

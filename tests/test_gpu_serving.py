@@ -35,6 +35,8 @@ def test_mix_equals_alone_and_reaches_tolerance(oracle_mod):
         mixed = srv.wait(tickets, timeout_s=WAIT_S)
         st = srv.stats()
     assert st["peak_bytes"] <= budget and st["peak_running"] > 1
+    # the small requests went through shared launches, several to a batch
+    assert st["batched"] >= 2 and st["batches"] < st["batched"]
     alone = []
     with g.Server(budget, max_slots=1) as srv:
         for A, B, _, _ in probs:
@@ -103,3 +105,45 @@ def test_borrowed_inputs_match_copied():
         res = srv.wait([t1, t2, t3], timeout_s=WAIT_S)
     np.testing.assert_array_equal(res[t1]["X"], res[t2]["X"])
     np.testing.assert_array_equal(res[t1]["X"], res[t3]["X"])
+
+
+def test_batched_requests_match_solo_slots(oracle_mod):
+    """A small request solved in a shared batch equals the same request
+    solved in a batch of its own, bit for bit, and both reach 1e-12; with
+    batching off the slot path also reaches it."""
+    cuda_or_fail()
+    g = lib()
+    probs = [p for p in problems() if p[0].shape[0] <= 1024]
+    with g.Server(8 << 30, max_slots=1, batch_max=64) as srv:
+        tickets = [srv.enqueue(A, B) for A, B, _, _ in probs]
+        together = srv.wait(tickets, timeout_s=WAIT_S)
+    with g.Server(8 << 30, max_slots=1) as srv:
+        solo = []
+        for A, B, _, _ in probs:
+            t = srv.enqueue(A, B)
+            solo.append(srv.wait([t], timeout_s=WAIT_S)[t])
+    with g.Server(8 << 30, max_slots=2, batch_n_max=-1) as srv:
+        slot = srv.wait([srv.enqueue(A, B) for A, B, _, _ in probs], timeout_s=WAIT_S)
+    for (A, B, Xt, kappa), t, rs in zip(probs, tickets, solo):
+        rt = together[t]
+        assert rt["status"] == "done" and rs["status"] == "done"
+        np.testing.assert_array_equal(rt["X"], rs["X"])
+        assert oracle_mod.backward_error(A, B, rt["X"]).max() <= 1e-12
+    assert all(r["status"] == "done" and r["batched"] == 0 and r["eta"] <= 1e-12 for r in slot.values())
+
+
+def test_batched_cache_hit(oracle_mod):
+    cuda_or_fail()
+    g = lib()
+    A, V1, V2, s = wl.householder_diag(400, 1e4, seed=15)
+    B1 = wl.matrix_normal(400, 3, seed=16)
+    B2 = wl.matrix_normal(400, 5, seed=17)
+    with g.Server(4 << 30, max_slots=1) as srv:
+        t1 = srv.enqueue(A, B1, matrix_id=77)
+        r1 = srv.wait([t1], timeout_s=WAIT_S)[t1]
+        t2 = srv.enqueue(A, B2, matrix_id=77)
+        r2 = srv.wait([t2], timeout_s=WAIT_S)[t2]
+        st = srv.stats()
+    assert r1["batched"] == 1 and r2["batched"] == 1
+    assert r1["cache_hit"] == 0 and r2["cache_hit"] == 1 and st["cache_entries"] == 1
+    assert oracle_mod.backward_error(A, B2, r2["X"]).max() <= 1e-12

@@ -15,11 +15,18 @@ def built():
     build.build()
 
 
-def req_bytes(n, nrhs):
-    """The server's own estimate (persistent + transient), to size budgets."""
-    per = n * n * 12 + n * 4 + 4096
+def req_bytes(n, nrhs, batched=None):
+    """The server's own estimate (persistent + transient), to size budgets.
+    batched: the shared-launch path (default for n <= 1024) or a slot."""
+    if batched is None:
+        batched = n <= 1024
     vs = n * nrhs
-    trans = 2 * vs * 8 + vs * (8 + 4 + 8 * (2 * 30 + 2)) + (304 * nrhs * 4 + 32 * 16 * nrhs + 16 * nrhs) * 8 + 4096 + n * 2048
+    per = n * n * 12 + n * 4 + 4096
+    if batched:
+        return per + vs * (3 * 8 + 4) + 16 * nrhs + 4096
+    per += n * (1024 + 4) + 4096
+    trans = 2 * vs * 8 + vs * (8 + 4 + 8 * (2 * 30 + 2)) + (304 * nrhs * 4 + 32 * 16 * nrhs + 16 * nrhs) * 8 + 4096 \
+        + n * (4 * 1040 + 2048)
     return per + trans
 
 
@@ -28,8 +35,10 @@ def small_problem(n, nrhs=1):
 
 
 def test_budget_never_exceeded_and_all_complete():
-    budget = 3 * req_bytes(400, 4)
-    with g.Server(budget, max_slots=4, dry_run=True) as srv:
+    """Every request on a slot of its own (batching off): the slot limit and
+    the budget hold."""
+    budget = 3 * req_bytes(400, 4, batched=False)
+    with g.Server(budget, max_slots=4, dry_run=True, batch_n_max=-1) as srv:
         sizes = [400, 100, 300, 50, 400, 250, 64, 128, 399, 200] * 3
         tickets = [srv.enqueue(*small_problem(n, 4)) for n in sizes]
         res = srv.wait(tickets)
@@ -98,3 +107,62 @@ def test_poll_retires_tickets():
         with pytest.raises(nat.LuError) as e:
             srv.poll(t)
         assert e.value.code == nat.LU_ENOTFOUND
+
+
+def test_small_requests_share_batches_within_budget():
+    """Small requests that queue while the batch worker is busy go out
+    together in the next shared launch; the budget still holds."""
+    budget = 12 * req_bytes(400, 4)
+    with g.Server(budget, max_slots=2, dry_run=True) as srv:
+        sizes = [400, 100, 300, 50, 400, 250, 64, 128, 399, 200] * 4
+        tickets = [srv.enqueue(*small_problem(n, 4)) for n in sizes]
+        res = srv.wait(tickets)
+        st = srv.stats()
+    assert all(r["status"] == "done" and r["batched"] == 1 for r in res.values())
+    assert st["completed"] == len(sizes) and st["batched"] == len(sizes)
+    assert st["batches"] < len(sizes)                    # some requests shared a launch
+    assert st["peak_bytes"] <= budget
+
+
+def test_batch_limit_and_large_requests_take_slots():
+    with g.Server(1 << 36, max_slots=2, dry_run=True, batch_max=3) as srv:
+        tickets = [srv.enqueue(*small_problem(200, 1)) for _ in range(10)]
+        big = srv.enqueue(*small_problem(1100, 1))
+        res = srv.wait(tickets + [big])
+        st = srv.stats()
+    assert res[big]["batched"] == 0 and res[big]["status"] == "done"
+    assert all(res[t]["batched"] == 1 for t in tickets)
+    assert st["batches"] >= 4                            # at most 3 per batch
+    assert st["batched"] == 10
+
+
+def test_batching_off():
+    with g.Server(1 << 34, max_slots=2, dry_run=True, batch_n_max=-1) as srv:
+        tickets = [srv.enqueue(*small_problem(64, 1)) for _ in range(5)]
+        res = srv.wait(tickets)
+        st = srv.stats()
+    assert all(r["batched"] == 0 for r in res.values())
+    assert st["batches"] == 0
+
+
+def test_bad_batch_config_rejected():
+    with pytest.raises(nat.LuError):
+        g.Server(1 << 30, dry_run=True, batch_n_max=2048)
+    with pytest.raises(nat.LuError):
+        g.Server(1 << 30, dry_run=True, batch_max=-1)
+
+
+def test_queue_bound_holds_per_path():
+    """max_queue bounds each path's queue: a backlog of large requests turns
+    further large ones away but still admits small ones."""
+    import time
+    with g.Server(1 << 38, max_slots=1, max_queue=2, dry_run=True) as srv:
+        first = srv.enqueue(*small_problem(1500, 1))      # occupies the only slot (~0.5 s)
+        time.sleep(0.05)
+        queued = [srv.enqueue(*small_problem(1200, 1)) for _ in range(2)]
+        with pytest.raises(nat.LuError) as e:
+            srv.enqueue(*small_problem(1200, 1))
+        assert e.value.code == nat.LU_EBUSY
+        smalls = [srv.enqueue(*small_problem(64, 1)) for _ in range(2)]
+        res = srv.wait(smalls + [first] + queued)
+    assert all(r["status"] == "done" for r in res.values())
