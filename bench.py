@@ -74,7 +74,7 @@ def parse():
                     help="order of the matrix the CPU oracle factors in each --impl reference step")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", choices=["lu64", "mixed", "batched", "serving", "cholesky", "lowp_gemm",
-                                           "lowp_factor"],
+                                           "lowp_factor", "batched_tune"],
                     default="lu64",
                     help="lu64: the FP64 factorization (default line); mixed: only the mixed-precision "
                          "refinement measurement; lowp_gemm: the tensor-core Schur update alone")
@@ -289,14 +289,21 @@ def run_mixed(a, dev, t_fp64_factor=None, warmup=1, steps=2, kappas=(1e2, 1e4, 1
 # batched: 8192 matrices, n log-uniform in [16, 1024], half with + n I
 # ---------------------------------------------------------------------------
 def run_batched(a, dev, count=8192, warmup=2, steps=3):
+    """8192 matrices, n log-uniform in [16, 1024], half with + n I, 1-8
+    right-hand sides each: the batched factorization and solve, one launch
+    each, timed with CUDA events on their stream (size and pointer arrays
+    built beforehand), then the same work replayed as one CUDA graph."""
     import torch
     import paper_2010_05975_gb300 as g
     import workloads as wl
     sizes = wl.batch_sizes(count, 16, 1024, seed=a.seed)
     flops = float(np.sum(2.0 * sizes.astype(np.float64) ** 3 / 3.0))
     out = {"count": count, "sizes": "log-uniform [16, 1024]", "sum_2n3_3": flops, "steps": steps,
-           "warmup": warmup, "cases": []}
-    stream = torch.cuda.current_stream(dev)
+           "warmup": warmup, "panel_widths": {"f64": [g.batched_panel_width(n, torch.float64)
+                                                      for n in (32, 64, 128, 256, 512, 1024)],
+                                              "f32": [g.batched_panel_width(n, torch.float32)
+                                                      for n in (32, 64, 128, 256, 512, 1024)]},
+           "cases": []}
     gen = torch.Generator(device=dev)
     for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
         gen.manual_seed(a.seed)
@@ -305,32 +312,94 @@ def run_batched(a, dev, count=8192, warmup=2, steps=3):
         mats0 = [pristine[offs[i]:offs[i + 1]].view(int(n), int(n)) for i, n in enumerate(sizes)]
         for i in range(1, count, 2):
             mats0[i].diagonal().add_(float(sizes[i]))
-        work = torch.empty_like(pristine)
-        mats = [work[offs[i]:offs[i + 1]].view(int(n), int(n)) for i, n in enumerate(sizes)]
-        rhs = [torch.ones(int(n), 1 + (i % 8), dtype=dt, device=dev) for i, n in enumerate(sizes)]
+        rhs0 = [torch.ones(int(n), 1 + (i % 8), dtype=dt, device=dev) for i, n in enumerate(sizes)]
+        bp = g.BatchedFactorSolve(mats0, rhs0)
         times, stimes = [], []
         for it in range(warmup + steps):
-            work.copy_(pristine)
-            torch.cuda.synchronize(dev)
+            bp.restore()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e2 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            pivs, info = g.lu_factor_batched(mats)
-            e1.record(stream)
-            g.lu_solve_batched(mats, pivs, rhs)
-            e2.record(stream)
+            e0.record(bp.stream)
+            bp.factor()
+            e1.record(bp.stream)
+            bp.solve()
+            e2.record(bp.stream)
             torch.cuda.synchronize(dev)
             if it >= warmup:
                 times.append(e0.elapsed_time(e1) / 1e3)
                 stimes.append(e1.elapsed_time(e2) / 1e3)
-        bad = int((info != 0).sum())
+        bad = int((bp.info != 0).sum())
+        bp.capture()
+        gtimes = []
+        for it in range(steps + 1):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(bp.stream)
+            bp.replay()
+            e1.record(bp.stream)
+            torch.cuda.synchronize(dev)
+            if it:
+                gtimes.append(e0.elapsed_time(e1))
         t = float(np.median(times))
         out["cases"].append({"dtype": name, "factor_ms": 1e3 * t, "matrices_per_s": count / t,
                              "tflops": flops / t / 1e12, "solve_ms": 1e3 * float(np.median(stimes)),
+                             "graph_replay_ms": float(np.median(gtimes)),
+                             "graph_note": "one graph: restore inputs, factor, solve",
                              "nonzero_info": bad})
-        del pristine, work, mats0, mats, rhs
+        del pristine, mats0, rhs0, bp
         torch.cuda.empty_cache()
+    return out
+
+
+def run_batched_tune(a, dev, per_class=2048, steps=3):
+    """Panel-width sweep of the batched factorization: for each size class
+    (n <= 32, 64, 128, 256, 512, 1024) and dtype, the factor time of
+    per_class matrices (log-uniform n inside the class, half with + n I) at
+    b = 8, 16, 32, and the fastest b."""
+    import torch
+    import paper_2010_05975_gb300 as g
+    import workloads as wl
+    bounds = [(8, 32), (33, 64), (65, 128), (129, 256), (257, 512), (513, 1024)]
+    out = {"per_class": per_class, "classes": []}
+    for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        best = []
+        for ci, (lo, hi) in enumerate(bounds):
+            sizes = wl.batch_sizes(per_class, lo, hi, seed=a.seed + ci)
+            gen = torch.Generator(device=dev)
+            gen.manual_seed(a.seed + ci)
+            mats = [torch.rand(int(n), int(n), dtype=dt, device=dev, generator=gen) * 2 - 1 for n in sizes]
+            for i in range(1, per_class, 2):
+                mats[i].diagonal().add_(float(sizes[i]))
+            rhs = [torch.ones(int(n), 1, dtype=dt, device=dev) for n in sizes]
+            bp = g.BatchedFactorSolve(mats, rhs)
+            flops = float(np.sum(2.0 * sizes.astype(np.float64) ** 3 / 3.0))
+            row = {"dtype": name, "n_range": [lo, hi], "ms": {}}
+            try:
+                for b in (8, 16, 32):
+                    g.set_batched_panel_widths(dt, [b] * 6)
+                    ts = []
+                    for it in range(steps + 1):
+                        bp.restore()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(bp.stream)
+                        bp.factor()
+                        e1.record(bp.stream)
+                        torch.cuda.synchronize(dev)
+                        if it:
+                            ts.append(e0.elapsed_time(e1))
+                    row["ms"][str(b)] = float(np.median(ts))
+            finally:
+                g.set_batched_panel_widths(dt, None)
+            bb = min(row["ms"], key=row["ms"].get)
+            row["best_b"] = int(bb)
+            row["best_tflops"] = flops / (row["ms"][bb] / 1e3) / 1e12
+            best.append(int(bb))
+            out["classes"].append(row)
+            del mats, rhs, bp
+            torch.cuda.empty_cache()
+        out[f"table_{name}"] = best
     return out
 
 
@@ -744,8 +813,18 @@ def run_ours(a):
         if info_h != 0:
             raise RuntimeError(f"lu_factor_host reported info={info_h}")
     te, _ = reduce_over_ranks(te, 0, world, dev)
+    # context: one pinned host -> device -> host round trip of the matrix alone
+    dtmp = torch.empty((n, n), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    dtmp.copy_(hwork, non_blocking=True)
+    hwork.copy_(dtmp, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    t_copy = time.perf_counter() - t0
+    del dtmp
     e2e = {"value": whole_job_value(world, ke, flops, te), "unit": UNIT, "steps": ke,
            "call": "lu_factor_host (C ABI, pinned host buffers)",
+           "copy_round_trip_s": t_copy, "host_buffer_pinned": bool(hwork.is_pinned()),
            "h2d_bytes_per_step": int(n * n * 8),
            "d2h_bytes_per_step": int(n * n * 8 + piv_h.numel() * 4 + 4)}
     del hwork
@@ -799,7 +878,7 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    elif a.workload in ("mixed", "batched", "serving", "cholesky", "lowp_gemm", "lowp_factor"):
+    elif a.workload in ("mixed", "batched", "serving", "cholesky", "lowp_gemm", "lowp_factor", "batched_tune"):
         import torch
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
         torch.cuda.set_device(dev)
@@ -818,8 +897,12 @@ def main():
             print(json.dumps({"metric": "Cholesky TFLOP/s (N^3/3)", "unit": "TFLOP/s",
                               "cholesky": run_cholesky(a, dev)}), flush=True)
         elif a.workload == "batched":
+            out = run_batched(a, dev)
             print(json.dumps({"metric": "batched LU matrices/s", "unit": "matrices/s",
-                              "batched": run_batched(a, dev)}), flush=True)
+                              "batched": out}), flush=True)
+        elif a.workload == "batched_tune":
+            print(json.dumps({"metric": "batched LU panel-width sweep", "unit": "ms",
+                              "batched_tune": run_batched_tune(a, dev)}), flush=True)
         else:
             print(json.dumps({"metric": "IR solves/s & p99 latency at 1e-12 bwd err", "unit": "solves/s",
                               "serving": run_serving(a, dev)}), flush=True)

@@ -269,13 +269,24 @@ int lu_residual_noalloc(int n, int nrhs, const double *A, int lda,
  *   info    device int[batch]: as lu_factor's info, or -1 when n is out of
  *           range, a pointer is null or lda < n (that matrix is skipped)
  *   dtype   LU_PREC_F64 or LU_PREC_F32
- * Panel width b = lu_batched_panel_width(n), leaf height h = 128.
+ * Panel width b = lu_batched_panel_width_dt(n, dtype), leaf height h = 128.
  */
 int lu_factor_batched(int batch, const int *n, void *const *A, const int *lda,
                       int *const *piv, int *info, int dtype, cudaStream_t stream);
 
-/* Panel width the batched factorization uses for an n x n matrix. */
+/* Panel width the batched factorization uses for an n x n binary64 matrix
+ * (lu_batched_panel_width) or for dtype LU_PREC_F64 / LU_PREC_F32
+ * (lu_batched_panel_width_dt; -2 for another dtype).  The width comes from a
+ * table over six size classes (n <= 32, <= 64, <= 128, <= 256, <= 512,
+ * <= 1024) whose defaults were measured on GB300. */
 int lu_batched_panel_width(int n);
+int lu_batched_panel_width_dt(int n, int dtype);
+
+/* Replace the size-class table of one dtype (count = 6 widths in 1..32) for
+ * the batched factorizations launched after the call, process-wide (a tuning
+ * sweep); widths = NULL restores the measured defaults.  Returns 0, -1 bad
+ * dtype, -2 a width out of range, -3 count != 6. */
+int lu_batched_set_panel_widths(int dtype, const int *widths, int count);
 
 /*
  * lu_solve_batched -- X = U^{-1} L^{-1} P B for each matrix of a batched

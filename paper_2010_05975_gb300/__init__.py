@@ -40,6 +40,8 @@ from .api import (  # noqa: F401
     lu_factor_batched,
     lu_solve_batched,
     batched_panel_width,
+    set_batched_panel_widths,
+    BatchedFactorSolve,
     prof_begin,
     prof_end,
     kernel_launch_count,

@@ -114,6 +114,8 @@ _SIGS = {
     "lu_factor_batched": ([I, P, P, P, P, P, I, P], I),
     "lu_solve_batched": ([I, P, P, P, P, P, P, P, I, P], I),
     "lu_batched_panel_width": ([I], I),
+    "lu_batched_panel_width_dt": ([I, I], I),
+    "lu_batched_set_panel_widths": ([I, P, I], I),
     "lu_residual_noalloc": ([I, I, P, I, P, I, P, I, P, I, P, P], I),
     "serve_create": ([ctypes.POINTER(serve_cfg), ctypes.POINTER(P)], I),
     "serve_enqueue": ([P, ctypes.POINTER(serve_req), ctypes.POINTER(ctypes.c_uint64)], I),

@@ -317,6 +317,92 @@ def lu_solve_batched(LUs, pivs, Bs, stream=None):
     return Bs
 
 
-def batched_panel_width(n: int) -> int:
+def batched_panel_width(n: int, dtype=torch.float64) -> int:
     """Panel width b the batched factorization uses for an n x n matrix."""
-    return int(nat.library().lu_batched_panel_width(int(n)))
+    prec = nat.LU_PREC_F32 if dtype == torch.float32 else nat.LU_PREC_F64
+    return int(nat.library().lu_batched_panel_width_dt(int(n), prec))
+
+
+def set_batched_panel_widths(dtype, widths=None) -> None:
+    """Replace the six size-class panel widths of the batched factorization
+    for dtype (torch.float64 / float32); None restores the defaults."""
+    prec = nat.LU_PREC_F32 if dtype == torch.float32 else nat.LU_PREC_F64
+    if widths is None:
+        nat.check("lu_batched_set_panel_widths", nat.library().lu_batched_set_panel_widths(prec, None, 6))
+        return
+    arr = (ctypes.c_int * len(widths))(*[int(w) for w in widths])
+    nat.check("lu_batched_set_panel_widths", nat.library().lu_batched_set_panel_widths(prec, arr, len(widths)))
+
+
+class BatchedFactorSolve:
+    """lu_factor_batched followed by lu_solve_batched over fixed lists of
+    matrices and right-hand sides, with the size and pointer arrays built
+    once: restore() copies the inputs from the caller's pristine tensors into
+    the work copies .A / .B, factor() and solve() are one C call each, and
+    capture() records restore + factor + solve as one CUDA graph that
+    replay() launches.  As / Bs are lists of CUDA tensors (float64 or
+    float32, n <= 1024, nrhs <= 8) that stay owned by the caller.  Everything
+    runs on self.stream."""
+
+    def __init__(self, As, Bs):
+        if not As or len(As) != len(Bs):
+            raise ValueError("need matching, non-empty lists of matrices and right-hand sides")
+        dt = As[0].dtype
+        if dt not in (torch.float64, torch.float32):
+            raise TypeError("batched matrices must be float64 or float32")
+        dev = As[0].device
+        self.A0, self.B0 = As, [B if B.dim() == 2 else B.view(-1, 1) for B in Bs]
+        for A, B in zip(self.A0, self.B0):
+            _require(A, "A", dt, 2)
+            _require(B, "B", dt, 2)
+        self.A = [a.clone() for a in self.A0]
+        self.B = [b.clone() for b in self.B0]
+        self.piv = [torch.empty(max(a.shape[0], 1), dtype=torch.int32, device=dev) for a in self.A]
+        self.info = torch.empty(len(self.A), dtype=torch.int32, device=dev)
+        i32 = dict(dtype=torch.int32, device=dev)
+        self._n = torch.tensor([a.shape[0] for a in self.A], **i32)
+        self._lda = torch.tensor([max(a.stride(0), 1) for a in self.A], **i32)
+        self._nr = torch.tensor([b.shape[1] for b in self.B], **i32)
+        self._ldb = torch.tensor([max(b.stride(0), 1) for b in self.B], **i32)
+        self._pa, self._pp, self._pb = _ptr_array(self.A, dev), _ptr_array(self.piv, dev), _ptr_array(self.B, dev)
+        self._prec = nat.LU_PREC_F64 if dt == torch.float64 else nat.LU_PREC_F32
+        self.stream = torch.cuda.Stream(device=dev)
+        self.stream.wait_stream(torch.cuda.current_stream(dev))
+        self.graph = None
+
+    def restore(self):
+        with torch.cuda.stream(self.stream):
+            for a, a0 in zip(self.A, self.A0):
+                a.copy_(a0)
+            for b, b0 in zip(self.B, self.B0):
+                b.copy_(b0)
+
+    def factor(self):
+        nat.check("lu_factor_batched", nat.library().lu_factor_batched(
+            len(self.A), self._n.data_ptr(), self._pa.data_ptr(), self._lda.data_ptr(), self._pp.data_ptr(),
+            self.info.data_ptr(), self._prec, ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def solve(self):
+        nat.check("lu_solve_batched", nat.library().lu_solve_batched(
+            len(self.A), self._n.data_ptr(), self._nr.data_ptr(), self._pa.data_ptr(), self._lda.data_ptr(),
+            self._pp.data_ptr(), self._pb.data_ptr(), self._ldb.data_ptr(), self._prec,
+            ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def capture(self):
+        """Record restore + factor + solve as one CUDA graph (after one plain
+        run, which sets kernel attributes and loads the device code)."""
+        self.restore()
+        self.factor()
+        self.solve()
+        self.stream.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream, capture_error_mode="thread_local"):
+            self.restore()
+            self.factor()
+            self.solve()
+        return self
+
+    def replay(self):
+        """One graph launch on self.stream (not synchronized)."""
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()

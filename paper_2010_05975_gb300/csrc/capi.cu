@@ -343,12 +343,18 @@ extern "C" int lu_factor_host(int m, int n, double* A, int lda, int* piv, int* i
     }
     int* dinfo = dpiv + kmax;
     int rc = 0;
-    if (cudaMemcpy2DAsync(dA, row, A, static_cast<size_t>(lda) * sizeof(double), row, m, cudaMemcpyHostToDevice,
-                          stream) != cudaSuccess)
+    // a contiguous matrix moves as one linear copy each way (a pitched copy
+    // of 8.6 GB may be split into row transfers)
+    const bool contig = (lda == n);
+    const size_t bytes = row * static_cast<size_t>(m);
+    if ((contig ? cudaMemcpyAsync(dA, A, bytes, cudaMemcpyHostToDevice, stream)
+                : cudaMemcpy2DAsync(dA, row, A, static_cast<size_t>(lda) * sizeof(double), row, m,
+                                    cudaMemcpyHostToDevice, stream)) != cudaSuccess)
         rc = LU_ELAUNCH;
     if (!rc) rc = factor_loop<double>(m, n, dA, n, dpiv, dinfo, b, h, SchurF64{}, stream);
-    if (!rc && (cudaMemcpy2DAsync(A, static_cast<size_t>(lda) * sizeof(double), dA, row, row, m,
-                                  cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+    if (!rc && ((contig ? cudaMemcpyAsync(A, dA, bytes, cudaMemcpyDeviceToHost, stream)
+                        : cudaMemcpy2DAsync(A, static_cast<size_t>(lda) * sizeof(double), dA, row, row, m,
+                                            cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
                 cudaMemcpyAsync(piv, dpiv, static_cast<size_t>(kmax) * sizeof(int), cudaMemcpyDeviceToHost,
                                 stream) != cudaSuccess ||
                 cudaMemcpyAsync(info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess))

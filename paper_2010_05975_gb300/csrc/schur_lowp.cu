@@ -501,63 +501,139 @@ __device__ __forceinline__ float block_max(float v, float* red) {
     return r;
 }
 
-// One CTA per 256-row block of L21 = A[r0 + 256 blk .., k : k+w).  Lq is
-// [M x 256], K-major; columns [w, kpad) hold zeros (kpad = w rounded up to a
-// 128-byte chunk), later columns are never read.  fp8: every row records the
-// exponent of its block's scale (eLrow), so that the row can later move (a
-// pivot swap of a deferred panel) and keep the scale it was rounded with.
+// Eight binary32 values from p (16-byte aligned when vec), zero at and past
+// column limit `lim` of the row.
+__device__ __forceinline__ void load8(const float* p, int c, int lim, bool vec, float (&v)[8]) {
+    if (vec && c + 8 <= lim) {
+        const float4 a = *reinterpret_cast<const float4*>(p + c), b = *reinterpret_cast<const float4*>(p + c + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = (c + i < lim) ? p[c + i] : 0.0f;
+    }
+}
+
+// 8 values -> 8 bf16 (16 bytes) or 8 e4m3 (8 bytes) at dst (aligned)
 template <bool kFp8>
-__global__ void __launch_bounds__(256) quantize_l21_kernel(const float* __restrict__ A, int lda, int r0, int M, int k,
-                                                           int w, int kpad, unsigned char* __restrict__ Lq,
+__device__ __forceinline__ void store8(unsigned char* dst, const float (&v)[8], int e) {
+    if constexpr (kFp8) {
+        uint32_t w[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            w[h] = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                w[h] |= static_cast<uint32_t>(__nv_cvt_float_to_fp8(ldexpf(v[4 * h + i], -e), __NV_SATFINITE, __NV_E4M3))
+                        << (8 * i);
+        }
+        *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+    } else {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(v[2 * i]));
+            const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(v[2 * i + 1]));
+            w[i] = lo | (hi << 16);
+        }
+        *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// L21 = A[r0 .. r0+M, k .. k+w) -> Lq [M x 256] (K-major), columns [w, kpad)
+// zero (kpad = w rounded up to a 128-byte chunk), later columns never read.
+// fp8: one power-of-two scale per 256-row block, counted from r0; every row
+// records its block's exponent (eLrow), so that the row can later move (a
+// pivot swap of a deferred panel) and keep the scale it was rounded with.
+// One CTA per 256-row block (fp8) or 64 rows (bf16); 8 consecutive K-values
+// per thread and step.
+template <bool kFp8>
+__global__ void __launch_bounds__(512) quantize_l21_kernel(const float* __restrict__ A, int lda, int r0, int M, int k,
+                                                           int w, int kpad, int vec, unsigned char* __restrict__ Lq,
                                                            int* __restrict__ eLrow) {
     __shared__ float red[32];
-    const int rb = blockIdx.x * kScaleTile;
-    const int nr = min(kScaleTile, M - rb);
+    constexpr int kElem = kFp8 ? 1 : 2;
+    constexpr int kRB = kFp8 ? kScaleTile : 64;     // rows per CTA (a whole scale block for fp8)
+    const int rb = blockIdx.x * kRB;
+    const int nr = min(kRB, M - rb);
+    const int tpr = kpad / 8;                       // threads per row
+    const int rpp = blockDim.x / tpr;               // rows per pass
+    const int tr = threadIdx.x / tpr, c = (threadIdx.x % tpr) * 8;
     int e = 0;
-    if (kFp8) {
+    if constexpr (kFp8) {
         float mx = 0.0f;
-        for (int i = threadIdx.x; i < nr * w; i += blockDim.x) mx = fmaxf(mx, fabsf(A[idx(r0 + rb + i / w, k + i % w, lda)]));
+        for (int i = tr; i < nr; i += rpp) {
+            float v[8];
+            load8(A + idx(r0 + rb + i, k, lda), c, w, vec != 0, v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) mx = fmaxf(mx, fabsf(v[q]));
+        }
         mx = block_max(mx, red);
         e = fp8_exponent(mx);
         for (int i = threadIdx.x; i < nr; i += blockDim.x) eLrow[rb + i] = e;
     }
-    for (int i = threadIdx.x; i < nr * kpad; i += blockDim.x) {
-        const int rr = i / kpad, kk = i % kpad;
-        const float x = kk < w ? A[idx(r0 + rb + rr, k + kk, lda)] : 0.0f;
-        store_q<kFp8>(Lq, static_cast<size_t>(rb + rr) * kTcK + kk, kFp8 ? ldexpf(x, -e) : x);
+    for (int i = tr; i < nr; i += rpp) {
+        float v[8];
+        load8(A + idx(r0 + rb + i, k, lda), c, w, vec != 0, v);
+        store8<kFp8>(Lq + (static_cast<size_t>(rb + i) * kTcK + c) * kElem, v, e);
     }
 }
 
-// One CTA per 256-column block of U12 = A[k : k+w, c0 + 256 blk ..).  UqT is
-// [N x 256] (transposed: K-major), K padded by zeros.
+// U12 = A[k .. k+w, c0 .. c0+N) -> UqT [N x 256] (transposed: K-major),
+// columns [w, kpad) zero.  fp8: one scale per 256 columns.  One CTA per 256
+// columns (fp8) or per 64 (bf16); 64-column chunks are staged transposed in
+// shared memory, then written 8 K-values per thread.
 template <bool kFp8>
-__global__ void __launch_bounds__(256) quantize_u12_kernel(const float* __restrict__ A, int lda, int k, int w, int c0,
-                                                           int N, int kpad, unsigned char* __restrict__ Uq,
+__global__ void __launch_bounds__(512) quantize_u12_kernel(const float* __restrict__ A, int lda, int k, int w, int c0,
+                                                           int N, int kpad, int vec, unsigned char* __restrict__ Uq,
                                                            int* __restrict__ expU) {
     __shared__ float red[32];
-    __shared__ float tile[32][kTcK + 1];
-    const int cb = blockIdx.x * kScaleTile;
-    const int nc = min(kScaleTile, N - cb);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* tile = reinterpret_cast<float*>(smem_raw);            // [64][kpad + 1]: tile[col][kk]
+    constexpr int kElem = kFp8 ? 1 : 2;
+    constexpr int kCols = kFp8 ? kScaleTile : 64;                // columns per CTA
+    const int cb = blockIdx.x * kCols;
+    const int nc = min(kCols, N - cb);
+    const int ts = kpad + 1;
     int e = 0;
-    if (kFp8) {
+    if constexpr (kFp8) {
         float mx = 0.0f;
-        for (int i = threadIdx.x; i < w * nc; i += blockDim.x) mx = fmaxf(mx, fabsf(A[idx(k + i / nc, c0 + cb + i % nc, lda)]));
+        // rows kk < w, 8 columns per thread
+        const int tpr = kCols / 8;
+        for (int i = threadIdx.x; i < w * tpr; i += blockDim.x) {
+            const int kk = i / tpr, cc = (i % tpr) * 8;
+            float v[8];
+            load8(A + idx(k + kk, c0 + cb, lda), cc, nc, vec != 0, v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) mx = fmaxf(mx, fabsf(v[q]));
+        }
         mx = block_max(mx, red);
         e = fp8_exponent(mx);
         if (threadIdx.x == 0) expU[blockIdx.x] = e;
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int cc = 0; cc < nc; cc += 32) {
-        // read 32 columns x w rows (coalesced along columns), transpose in smem
-        for (int kk = warp; kk < kpad; kk += 8)
-            tile[lane][kk] = (kk < w && cc + lane < nc) ? A[idx(k + kk, c0 + cb + cc + lane, lda)] : 0.0f;
-        __syncthreads();
-        for (int i = threadIdx.x; i < 32 * kpad; i += blockDim.x) {
-            const int col = i / kpad, kk = i % kpad;
-            if (cc + col < nc) {
-                const float x = tile[col][kk];
-                store_q<kFp8>(Uq, static_cast<size_t>(cb + cc + col) * kTcK + kk, kFp8 ? ldexpf(x, -e) : x);
+    for (int ch = 0; ch < nc; ch += 64) {
+        const int ncc = min(64, nc - ch);
+        // rows kk < kpad of the 64-column chunk, transposed (zero past w)
+        for (int i = threadIdx.x; i < kpad * 8; i += blockDim.x) {
+            const int kk = i / 8, cc = (i % 8) * 8;
+            float v[8];
+            if (kk < w) {
+                load8(A + idx(k + kk, c0 + cb + ch, lda), cc, ncc, vec != 0, v);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = 0.0f;
             }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) tile[(cc + q) * ts + kk] = v[q];
+        }
+        __syncthreads();
+        const int tpc = kpad / 8;                               // threads per column
+        for (int i = threadIdx.x; i < ncc * tpc; i += blockDim.x) {
+            const int col = i / tpc, kk = (i % tpc) * 8;
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = tile[col * ts + kk + q];
+            store8<kFp8>(Uq + (static_cast<size_t>(cb + ch + col) * kTcK + kk) * kElem, v, e);
         }
         __syncthreads();
     }
@@ -637,13 +713,14 @@ int quantize_l21(const float* A, int lda, int m, int k, int w, bool fp8, void* L
     const int r0 = k + w, M = m - r0;
     if (M <= 0) return 0;
     const int kpad = lowp_kpad(w, fp8);
+    const int vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda & 3) == 0 && (k & 3) == 0) ? 1 : 0;
     {
         ProfScope ps(LU_PROF_OTHER, s);
         if (fp8)
-            quantize_l21_kernel<true><<<cdiv(M, kScaleTile), 256, 0, s>>>(A, lda, r0, M, k, w, kpad,
+            quantize_l21_kernel<true><<<cdiv(M, kScaleTile), 512, 0, s>>>(A, lda, r0, M, k, w, kpad, vec,
                                                                            static_cast<unsigned char*>(Lq), eLrow);
         else
-            quantize_l21_kernel<false><<<cdiv(M, kScaleTile), 256, 0, s>>>(A, lda, r0, M, k, w, kpad,
+            quantize_l21_kernel<false><<<cdiv(M, 64), 512, 0, s>>>(A, lda, r0, M, k, w, kpad, vec,
                                                                             static_cast<unsigned char*>(Lq), eLrow);
         count_launches(1);
     }
@@ -656,14 +733,19 @@ int quantize_u12(const float* A, int lda, int k, int w, int c0, int c1, bool fp8
     const int N = c1 - c0;
     if (N <= 0) return 0;
     const int kpad = lowp_kpad(w, fp8);
+    const int vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda & 3) == 0 && (c0 & 3) == 0) ? 1 : 0;
+    const size_t smem = static_cast<size_t>(64) * (kpad + 1) * sizeof(float);
     {
         ProfScope ps(LU_PROF_OTHER, s);
-        if (fp8)
-            quantize_u12_kernel<true><<<cdiv(N, kScaleTile), 256, 0, s>>>(A, lda, k, w, c0, N, kpad,
-                                                                           static_cast<unsigned char*>(Uq), expU);
-        else
-            quantize_u12_kernel<false><<<cdiv(N, kScaleTile), 256, 0, s>>>(A, lda, k, w, c0, N, kpad,
-                                                                            static_cast<unsigned char*>(Uq), expU);
+        if (fp8) {
+            if (int rc_ = smem_attr(quantize_u12_kernel<true>, smem)) return rc_;
+            quantize_u12_kernel<true><<<cdiv(N, kScaleTile), 512, smem, s>>>(A, lda, k, w, c0, N, kpad, vec,
+                                                                              static_cast<unsigned char*>(Uq), expU);
+        } else {
+            if (int rc_ = smem_attr(quantize_u12_kernel<false>, smem)) return rc_;
+            quantize_u12_kernel<false><<<cdiv(N, 64), 512, smem, s>>>(A, lda, k, w, c0, N, kpad, vec,
+                                                                       static_cast<unsigned char*>(Uq), expU);
+        }
         count_launches(1);
     }
     LU_LAUNCHED();

@@ -150,3 +150,27 @@ def test_wait_deadline_config_host_side(native):
     finally:
         assert lib.lu_test_wait_config(SOLVE, 0, 0) == 0
     assert lib.lu_wait_deadline_ns(SOLVE) == 4 * 10 ** 9
+
+
+def test_batched_width_table_host_side(native):
+    """The batched size-class table: lookups, a replacement, its checks and
+    the restore (host-side state only)."""
+    import torch
+    lib = native.library()
+    F64, F32 = native.LU_PREC_F64, native.LU_PREC_F32
+    assert lib.lu_batched_panel_width_dt(100, 7) == -2
+    default = [native.batched_panel_width(n, torch.float32) for n in (20, 50, 100, 200, 400, 1000)]
+    arr = (ctypes.c_int * 6)(8, 8, 16, 16, 32, 32)
+    assert lib.lu_batched_set_panel_widths(9, arr, 6) == -1
+    assert lib.lu_batched_set_panel_widths(F32, arr, 5) == -3
+    bad = (ctypes.c_int * 6)(8, 8, 16, 16, 33, 32)
+    assert lib.lu_batched_set_panel_widths(F32, bad, 6) == -2
+    try:
+        assert lib.lu_batched_set_panel_widths(F32, arr, 6) == 0
+        got = [lib.lu_batched_panel_width_dt(n, F32) for n in (1, 32, 33, 64, 65, 128, 129, 256, 257, 512, 513, 1024)]
+        assert got == [8, 8, 8, 8, 16, 16, 16, 16, 32, 32, 32, 32]
+        # the binary64 table is separate
+        assert lib.lu_batched_panel_width_dt(20, F64) == lib.lu_batched_panel_width(20)
+    finally:
+        assert lib.lu_batched_set_panel_widths(F32, None, 6) == 0
+    assert [native.batched_panel_width(n, torch.float32) for n in (20, 50, 100, 200, 400, 1000)] == default

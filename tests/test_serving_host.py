@@ -166,3 +166,18 @@ def test_queue_bound_holds_per_path():
         smalls = [srv.enqueue(*small_problem(64, 1)) for _ in range(2)]
         res = srv.wait(smalls + [first] + queued)
     assert all(r["status"] == "done" for r in res.values())
+
+
+def test_budget_accounting_matches_cache_entries():
+    """With every request done, the bytes the server still charges are
+    exactly its cached entries' (the factors kept per matrix id)."""
+    with g.Server(1 << 36, max_slots=2, dry_run=True) as srv:
+        ids = [11, 12, 13]
+        ts = [srv.enqueue(*small_problem(300, 2), matrix_id=i) for i in ids]          # batched path
+        ts += [srv.enqueue(*small_problem(1100, 1), matrix_id=20 + i) for i in range(2)]   # slot path
+        ts += [srv.enqueue(*small_problem(200, 1)) for _ in range(3)]                 # no cache
+        srv.wait(ts)
+        st = srv.stats()
+    assert st["cache_entries"] == 5
+    assert st["used_bytes"] == 3 * (300 * 300 * 12 + 300 * 4 + 4096) + \
+        2 * (1100 * 1100 * 12 + 1100 * 4 + 4096 + 1100 * (1024 + 4) + 4096)
