@@ -142,7 +142,7 @@ __device__ __forceinline__ void gepp_bar(int id, int nthreads) {
 
 // Row r of W: its trailing columns from j0 (rounded down to 16 bytes; the
 // columns before j0 are written back unchanged), chunks i = s, s+S, ...,
-// two in flight, each taking the panel's KB updates in pivot order.  Pivot
+// four in flight, each taking the panel's KB updates in pivot order.  Pivot
 // row q is row rq[q] of Ub (stride us).
 template <typename T, bool FULL>
 __device__ __forceinline__ void gepp_rank_row(T* W, int ws, int r, int s, int S, int j0, int w,
@@ -150,46 +150,50 @@ __device__ __forceinline__ void gepp_rank_row(T* W, int ws, int r, int s, int S,
                                               const int (&rq)[kGeppKB], int kb, unsigned zm) {
     constexpr int KB = kGeppKB;
     constexpr int V = 16 / sizeof(T);
+    constexpr int NF = 4;                               // chunks in flight
     const int cb = j0 & ~(V - 1);
     const int nch = (w - cb + V - 1) / V;
     T* row = W + static_cast<size_t>(r) * ws;
-    for (int i = s; i < nch; i += 2 * S) {
-        const int jA = cb + V * i, jB = jA + V * S;
-        const bool hasB = i + S < nch;
-        T a[V], b[V], a0[V], b0[V];
-        gepp_ld16(row + jA, a);
-        if (hasB) {
-            gepp_ld16(row + jB, b);
-        } else {
+    for (int i = s; i < nch; i += NF * S) {
+        T a[NF][V], a0[NF][V];
+        int jj[NF];
+        bool has[NF];
 #pragma unroll
-            for (int v = 0; v < V; ++v) b[v] = T(0);
-        }
+        for (int f = 0; f < NF; ++f) {
+            jj[f] = cb + V * (i + f * S);
+            has[f] = (i + f * S) < nch;
+            if (has[f]) {
+                gepp_ld16(row + jj[f], a[f]);
+            } else {
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            a0[v] = a[v];
-            b0[v] = b[v];
+                for (int v = 0; v < V; ++v) a[f][v] = T(0);
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) a0[f][v] = a[f][v];
         }
 #pragma unroll
         for (int q = 0; q < KB; ++q) {
             if (FULL || (q < kb && !((zm >> q) & 1u))) {
                 const T* up = Ub + static_cast<size_t>(rq[q]) * us;
-                T ua[V], ub[V];
-                gepp_ld16(up + jA, ua);
-                if (hasB) gepp_ld16(up + jB, ub);
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    a[v] = fma(-mr[q], ua[v], a[v]);
-                    if (hasB) b[v] = fma(-mr[q], ub[v], b[v]);
+                for (int f = 0; f < NF; ++f) {
+                    if (has[f]) {
+                        T u[V];
+                        gepp_ld16(up + jj[f], u);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) a[f][v] = fma(-mr[q], u[v], a[f][v]);
+                    }
                 }
             }
         }
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            if (jA + v < j0 || jA + v >= w) a[v] = a0[v];
-            if (jB + v >= w) b[v] = b0[v];
+        for (int f = 0; f < NF; ++f) {
+            if (!has[f]) continue;
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (jj[f] + v < j0 || jj[f] + v >= w) a[f][v] = a0[f][v];
+            gepp_st16(row + jj[f], a[f]);
         }
-        gepp_st16(row + jA, a);
-        if (hasB) gepp_st16(row + jB, b);
     }
 }
 
@@ -354,6 +358,174 @@ __device__ void node_gepp_blocked(T* W, int ws, int nr, int w, int ns, const int
         }
         __syncthreads();
     }
+}
+
+// The same selection with a lookahead inside the node, for a CTA of at
+// least 2 x 256 threads and nr <= 256 rows.  The first warps own the rows
+// (one per thread, as above); warps 8.. form the update group, thread u of
+// which also works on row u.  Per panel p (columns [c0, c0 + kb)):
+//   row warps     the column chain of panel p on the slab they updated
+//                 last; then the pivot rows' trailing columns (the
+//                 triangle); then panel p's rank-KB update of their own rows
+//                 on the next slab [j0, j0 + KB) only;
+//   update warps  meanwhile, panel p-1's rank-KB update of every row not
+//                 chosen by then, on the columns after that slab.
+// Two block barriers per panel order the phases: every element still takes
+// its pivots' updates in ascending order (the near slab of panel p after the
+// far part of panel p-1 has reached it), each multiplier is one IEEE
+// division, so rows, multipliers and factors are node_gepp_blocked's bit
+// for bit.  Named barrier 1 is used among the row warps.
+// End of the near slab after column j0: KB columns, rounded up to a 16-byte
+// chunk so that the row warps' near update and the update warps' far update
+// (which run at the same time, each rewriting whole chunks) never share a
+// chunk.
+__device__ __forceinline__ int near_end(int j0, int w) { return min((j0 + kGeppKB + 3) & ~3, w); }
+
+template <typename T>
+__device__ void node_gepp_la(T* W, int ws, int nr, int w, int ns, const int* ids, int* ord, int* winp, int* lrow,
+                             GeppSlots<T>& sl, unsigned* zmp, int* zero_first) {
+    constexpr int KB = kGeppKB;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwo = (nr + 31) >> 5;                   // row warps
+    const bool rowgrp = warp < nwo;
+    const bool updgrp = tid >= 256;
+    const int u = tid - 256;                           // update-group row
+    const bool own = tid < nr;
+    T* const wr = W + static_cast<size_t>(own ? tid : 0) * ws;
+    bool live = own && ord[tid] < 0;
+    const int myid = own ? ids[tid] : INT_MAX;
+    if (ns <= 0) {
+        __syncthreads();
+        return;
+    }
+    const int npan = (ns + KB - 1) / KB;
+    T P[KB];                                           // row warps: the panel's values, then multipliers
+    for (int p = 0; p <= npan; ++p) {
+        const int c0 = p * KB;
+        const int kb = p < npan ? min(KB, ns - c0) : 0;
+        const int j0 = c0 + kb;
+        // ---------------- update warps: panel p-1, far columns ----------------
+        if (updgrp && p >= 1 && u < nr) {
+            const int pc0 = (p - 1) * KB;
+            const int pkb = min(KB, ns - pc0);
+            const int far0 = near_end(pc0 + pkb, w);  // after the slab the row warps updated
+            const int o = ord[u];                       // -1, or a step of panel p or later: still to update
+            if (far0 < w && (o < 0 || o >= pc0 + KB)) {
+                const unsigned pzm = zmp[(p - 1) & 1];
+                int prq[KB];
+#pragma unroll
+                for (int q = 0; q < KB; ++q) prq[q] = (q < pkb) ? lrow[pc0 + q] : 0;
+                T mr[KB];
+                gepp_vload(W + static_cast<size_t>(u) * ws + pc0, mr);
+                if (pkb == KB && pzm == 0)
+                    gepp_rank_row<T, true>(W, ws, u, 0, 1, far0, w, mr, W, ws, prq, pkb, pzm);
+                else
+                    gepp_rank_row<T, false>(W, ws, u, 0, 1, far0, w, mr, W, ws, prq, pkb, pzm);
+            }
+        }
+        int rq[KB];
+        unsigned zm = 0;
+        // ---------------- row warps: column chain of panel p ----------------
+        if (p < npan && rowgrp) {
+            if (own) {
+                gepp_vload(wr + c0, P);
+            } else {
+#pragma unroll
+                for (int k = 0; k < KB; ++k) P[k] = T(0);
+            }
+            int khi;
+            unsigned klo;
+            gepp_key(P[0], live, khi, klo);
+            int chosen = -1;
+#pragma unroll
+            for (int k = 0; k < KB; ++k) {
+                rq[k] = 0;
+                if (k < kb) {
+                    const int c = c0 + k;
+                    const int buf = c & 1;
+                    int mhi;
+                    unsigned mlo;
+                    const int wl = gepp_warp_best<T>(khi, klo, lane, mhi, mlo);
+                    if (lane == wl) {
+                        sl.key[buf][warp] = mhi;
+                        sl.key_lo[buf][warp] = mlo;
+                        sl.row[buf][warp] = tid;
+                        gepp_vstore(&sl.val[buf][warp][0], P);
+                    }
+                    gepp_bar(1, nwo * 32);
+                    const int phi = lane < nwo ? sl.key[buf][lane] : -1;
+                    const unsigned plo = lane < nwo ? sl.key_lo[buf][lane] : 0u;
+                    const int prow = lane < nwo ? sl.row[buf][lane] : INT_MAX;
+                    const int ghi = __reduce_max_sync(0xffffffffu, phi);
+                    bool cand = (phi == ghi);
+                    if (sizeof(T) == 8) {
+                        const unsigned glo = __reduce_max_sync(0xffffffffu, cand ? plo : 0u);
+                        cand = cand && (plo == glo);
+                    }
+                    const int lr = __reduce_min_sync(0xffffffffu, cand ? prow : INT_MAX);
+                    T U[KB];
+                    gepp_vload(&sl.val[buf][lr >> 5][0], U);
+                    rq[k] = lr;
+                    const T pv = U[k];
+                    const bool pz = (pv == T(0));
+                    if (pz) zm |= 1u << k;
+                    const bool win = live && (tid == lr);
+                    if (win) chosen = k;
+                    const bool upd = live && !win && !pz;
+                    const T l = P[k] / (upd ? pv : T(1));
+                    if (upd) P[k] = l;
+#pragma unroll
+                    for (int j = k + 1; j < KB; ++j)
+                        if (j < kb && upd) P[j] = fma(-l, U[j], P[j]);
+                    live = live && !win;
+                    gepp_key(P[(k + 1) < KB ? k + 1 : KB - 1], live && k + 1 < kb, khi, klo);
+                }
+            }
+            if (chosen >= 0) {
+                ord[tid] = c0 + chosen;
+                winp[c0 + chosen] = myid;
+                lrow[c0 + chosen] = tid;
+            }
+            if (chosen >= 0 || live) gepp_store_panel(wr + c0, P, kb);
+            if (tid == 0) {
+                zmp[p & 1] = zm;
+                if (zero_first != nullptr && zm != 0 && *zero_first < 0) *zero_first = c0 + __ffs(zm) - 1;
+            }
+        }
+        __syncthreads();
+        if (p == npan) break;
+        // ---------------- row warps: triangle of panel p (the pivot rows'
+        // multipliers are in W since the chain stored them) ----------------
+        if (rowgrp && kb > 1) {
+            for (int j = j0 + tid; j < w; j += nwo * 32) {
+                T uu[KB];
+#pragma unroll
+                for (int q = 0; q < KB; ++q) uu[q] = (q < kb) ? W[static_cast<size_t>(rq[q]) * ws + j] : T(0);
+#pragma unroll
+                for (int q = 1; q < KB; ++q) {
+                    if (q < kb) {
+#pragma unroll
+                        for (int qq = 0; qq < KB; ++qq)
+                            if (qq < q && !((zm >> qq) & 1u))
+                                uu[q] = fma(-W[static_cast<size_t>(rq[q]) * ws + c0 + qq], uu[qq], uu[q]);
+                    }
+                }
+#pragma unroll
+                for (int q = 1; q < KB; ++q)
+                    if (q < kb) W[static_cast<size_t>(rq[q]) * ws + j] = uu[q];
+            }
+        }
+        __syncthreads();
+        // ---------------- row warps: panel p on the next slab ----------------
+        if (rowgrp && live && j0 < w) {
+            const int jn = near_end(j0, w);
+            if (kb == KB && zm == 0)
+                gepp_rank_row<T, true>(W, ws, tid, 0, 1, j0, jn, P, W, ws, rq, kb, zm);
+            else
+                gepp_rank_row<T, false>(W, ws, tid, 0, 1, j0, jn, P, W, ws, rq, kb, zm);
+        }
+    }
+    __syncthreads();
 }
 
 }  // namespace lu

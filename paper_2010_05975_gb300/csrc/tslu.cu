@@ -212,7 +212,13 @@ __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs
     const int ns = min(nr, w);
     if constexpr (MODE == 1) {
         __shared__ GeppSlots<T> gslots;
-        node_gepp_blocked<T>(W, ws, nloc, w, ns, ids, ord, winp, lrow, gslots, &s_zero);
+        if (sizeof(T) == 4 && blockDim.x >= 512 && nloc <= 256) {
+            // binary32 nodes: the update warps run one panel behind the row warps
+            __shared__ unsigned s_zmp[2];
+            node_gepp_la<T>(W, ws, nloc, w, ns, ids, ord, winp, lrow, gslots, s_zmp, &s_zero);
+        } else {
+            node_gepp_blocked<T>(W, ws, nloc, w, ns, ids, ord, winp, lrow, gslots, &s_zero);
+        }
     } else if constexpr (MODE == 2) {
         __shared__ GeppClusterSlot<T> cslot;
         node_gepp_cluster<T>(W, ws, nloc, a.R, a.C, q, w, ns, ids, ord, winp, Ub, cslot, q == 0 ? &s_zero : nullptr,
