@@ -85,7 +85,7 @@ __device__ void node_select(Smem<T>& sm, const T* A, int lda, int k, int w, int 
         W[r * ws + j] = A[idx(sm.ids[r], k + j, lda)];
     }
     __syncthreads();
-    node_gepp_blocked<T>(W, ws, nr, w, min(nr, w), sm.ids, sm.ord, out, sm.lrow, sm.gs,
+    node_gepp_blocked<T, false>(W, ws, nr, w, min(nr, w), sm.ids, sm.ord, out, sm.lrow, sm.gs,
                          root ? &sm.zero_first : nullptr);
     if (root)
         for (int e = tid; e < nr * w; e += blockDim.x) {
@@ -317,7 +317,7 @@ __device__ void schur(Smem<T>& sm, T* A, int lda, int n, int k, int w) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) batched_lu_kernel(int batch, const int* __restrict__ ns,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) batched_lu_kernel(int batch, const int* __restrict__ ns,
                                                               T* const* __restrict__ As, const int* __restrict__ ldas,
                                                               int* const* __restrict__ pivs, int* __restrict__ info,
                                                               const int* __restrict__ order, int* __restrict__ counter,

@@ -212,7 +212,7 @@ __device__ __forceinline__ void gepp_rank_row(T* W, int ws, int r, int s, int S,
 // Requires nr <= blockDim.x (a multiple of 32) and ns <= min(nr, w).  The
 // caller has made W, ids and ord visible to the block (a barrier); the
 // function ends with a block barrier.  Named barrier 1 is used.
-template <typename T>
+template <typename T, bool LREG = (sizeof(T) == 4)>
 __device__ void node_gepp_blocked(T* W, int ws, int nr, int w, int ns, const int* ids, int* ord, int* winp,
                                   int* lrow, GeppSlots<T>& sl, int* zero_first) {
     constexpr int KB = kGeppKB;
@@ -246,9 +246,10 @@ __device__ void node_gepp_blocked(T* W, int ws, int nr, int w, int ns, const int
             unsigned zm = 0;
             int chosen = -1;
             int rq[KB];
-            // binary32 keeps the step-q pivot row's multipliers L[q][qq] (qq < q)
-            // in registers; binary64 reads them back from W.
-            constexpr bool kLreg = sizeof(T) == 4;
+            // LREG (the binary32 default) keeps the step-q pivot row's
+            // multipliers L[q][qq] (qq < q) in registers; otherwise they are
+            // read back from W.
+            constexpr bool kLreg = LREG;
             T L[kLreg ? KB : 1][KB];
 #pragma unroll
             for (int k = 0; k < KB; ++k) {
