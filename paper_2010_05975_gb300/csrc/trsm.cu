@@ -78,70 +78,115 @@ __global__ void __launch_bounds__(256) trsm_u12_kernel(E* __restrict__ A, int ld
 // binary32: one thread per row (column), left-looking in register blocks.
 // ---------------------------------------------------------------------------
 constexpr int kRowCta = 64;        // rows of A21 (columns of A12) per CTA, one per thread
-constexpr int kTileStride = kRowCta + 1;
 constexpr int kStrip = 64;         // triangle columns (rows) staged per strip
-constexpr int kStripStride = kStrip + 4;   // 16-byte rows; staging writes spread over banks
 constexpr int kRb = 16;            // register block
 
 __host__ __device__ constexpr int trsm_wp(int w) { return (w + kRb - 1) / kRb * kRb; }
+// Row pitches (floats): a whole number of 16-byte chunks plus one, so that
+// eight consecutive rows' 16-byte reads fall in distinct bank groups.
+__host__ __device__ constexpr int trsm_pitch(int cols) { return (cols + 3) / 4 * 4 + 4; }
 
-// Shared memory: the strip S[j][c'] (stride kStripStride) then the tile
-// T[j][r] (stride kTileStride, wp rows).
-inline size_t trsm_rows_smem(int w) {
-    return (static_cast<size_t>(w) * kStripStride + static_cast<size_t>(trsm_wp(w)) * kTileStride) * sizeof(float);
+// Shared memory: the tile (kRowCta rows of wp columns for L21, wp rows of
+// kRowCta columns for U12) and one strip of the triangle.
+inline size_t trsm_l21_smem(int w) {
+    return (static_cast<size_t>(kRowCta) * trsm_pitch(trsm_wp(w)) +
+            static_cast<size_t>(w) * trsm_pitch(kStrip)) * sizeof(float);
+}
+inline size_t trsm_u12_smem(int w) {
+    return (static_cast<size_t>(trsm_wp(w)) * trsm_pitch(kRowCta) +
+            static_cast<size_t>(kStrip) * trsm_pitch(trsm_wp(w))) * sizeof(float);
 }
 
-// acc[i] = fma(-x, v[i], acc[i]) for one register block, v 16-byte aligned.
-__device__ __forceinline__ void trsm_axpy16(float (&acc)[kRb], float x, const float* v) {
-#pragma unroll
-    for (int q = 0; q < kRb / 4; ++q) {
-        const float4 u = *reinterpret_cast<const float4*>(v + 4 * q);
-        acc[4 * q + 0] = fmaf(-x, u.x, acc[4 * q + 0]);
-        acc[4 * q + 1] = fmaf(-x, u.y, acc[4 * q + 1]);
-        acc[4 * q + 2] = fmaf(-x, u.z, acc[4 * q + 2]);
-        acc[4 * q + 3] = fmaf(-x, u.w, acc[4 * q + 3]);
+// 16-byte asynchronous copy global -> shared; bytes < 16 reads that many
+// and zero-fills the rest (0: nothing is read).
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, int bytes) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Stage rows x cols of a row-major global block (leading dimension ld) into
+// shared memory (pitch floats per row), zero outside [0, vrows) x [0, vcols).
+// vec: the global rows start 16-byte aligned, so 16-byte asynchronous copies
+// are used; otherwise plain loads.
+__device__ __forceinline__ void trsm_stage(float* dst, int pitch, const float* src, size_t ld, int rows, int cols,
+                                           int vrows, int vcols, bool vec) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (vec) {
+        const int cq = (cols + 3) / 4;
+        for (int e = tid; e < rows * cq; e += nt) {
+            const int r = e / cq, c = 4 * (e - r * cq);
+            const int bytes = (r < vrows) ? 4 * max(0, min(4, vcols - c)) : 0;
+            cp_async16(dst + static_cast<size_t>(r) * pitch + c, bytes ? src + r * ld + c : src, bytes);
+        }
+        cp_async_wait_all();
+    } else {
+        for (int e = tid; e < rows * cols; e += nt) {
+            const int r = e / cols, c = e - r * cols;
+            dst[static_cast<size_t>(r) * pitch + c] = (r < vrows && c < vcols) ? src[r * ld + c] : 0.f;
+        }
     }
 }
 
-// L21 = A21 * U^{-1}.  Thread r owns row r0 + r; its solved values replace
-// the tile's in place.  Per strip of kStrip columns [s0, s1) the CTA stages
-// U[0:s1, s0:s1) (upper part; zeros below the diagonal), then each thread
-// takes its row's register blocks of the strip: the updates of every earlier
-// column j (from the tile), then the block's own columns in order, each
-// finished by its division.  Per element that is fma over j ascending, then
-// the division: the sequence of the right-looking sweep.
+// acc[i] = fma(-x[q], v_q[i], acc[i]) for q = 0..3 in order, v_q = v + q * vp
+// (16-byte aligned rows of the staged triangle).
+__device__ __forceinline__ void trsm_axpy16x4(float (&acc)[kRb], const float4 x, const float* v, int vp) {
+    const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int h = 0; h < kRb / 4; ++h) {
+            const float4 u = *reinterpret_cast<const float4*>(v + q * vp + 4 * h);
+            acc[4 * h + 0] = fmaf(-xs[q], u.x, acc[4 * h + 0]);
+            acc[4 * h + 1] = fmaf(-xs[q], u.y, acc[4 * h + 1]);
+            acc[4 * h + 2] = fmaf(-xs[q], u.z, acc[4 * h + 2]);
+            acc[4 * h + 3] = fmaf(-xs[q], u.w, acc[4 * h + 3]);
+        }
+    }
+}
+
+// L21 = A21 * U^{-1}.  Thread r owns row r0 + r, kept in the tile T[r][j]
+// (row-major), whose solved values replace the inputs in place.  Per strip
+// of kStrip columns [s0, s1) the CTA stages U[0:s1, s0:s1) (only entries on
+// or above the diagonal are read), then each thread takes its row's
+// register blocks of the strip: the updates of every earlier column j, four
+// at a time from one 16-byte read of its row, then the block's own columns
+// in order, each finished by its division.  Per element that is fma over j
+// ascending, then the division: the sequence of the right-looking sweep.
 __global__ void __launch_bounds__(kRowCta) trsm_l21_rows_kernel(float* __restrict__ A, int lda, int m, int k, int w,
-                                                                const float* __restrict__ U, int ldu) {
+                                                                const float* __restrict__ U, int ldu, int vec) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* S = reinterpret_cast<float*>(smem_raw);
-    float* T = S + static_cast<size_t>(w) * kStripStride;
     const int wp = trsm_wp(w);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tp = trsm_pitch(wp), sp = trsm_pitch(kStrip);
+    float* T = reinterpret_cast<float*>(smem_raw);
+    float* S = T + static_cast<size_t>(kRowCta) * tp;
+    const int tid = threadIdx.x;
     const int r0 = k + w + blockIdx.x * kRowCta;
     const int nrow = min(kRowCta, m - r0);
-    for (int r = warp; r < kRowCta; r += kRowCta / 32) {
-        const bool ok = r < nrow;
-        for (int j = lane; j < wp; j += 32)
-            T[j * kTileStride + r] = (ok && j < w) ? A[idx(r0 + r, k + j, lda)] : 0.f;
-    }
+    trsm_stage(T, tp, A + idx(r0, k, lda), lda, kRowCta, wp, nrow, w, vec != 0);
+    float* Tr = T + static_cast<size_t>(tid) * tp;
     for (int s0 = 0; s0 < w; s0 += kStrip) {
         const int s1 = min(s0 + kStrip, w);
-        __syncthreads();                                   // the previous strip is no longer read
-        for (int e = tid; e < s1 * kStrip; e += kRowCta) {
-            const int j = e / kStrip, c = s0 + e % kStrip;
-            S[j * kStripStride + (c - s0)] = (c < s1 && c >= j) ? U[idx(j, c, ldu)] : 0.f;
-        }
+        __syncthreads();                                   // the tile is in; the previous strip is no longer read
+        trsm_stage(S, sp, U + idx(0, s0, ldu), ldu, s1, kStrip, s1, s1 - s0, vec != 0);
         __syncthreads();
         for (int c0 = s0; c0 < s1; c0 += kRb) {
             float acc[kRb];
 #pragma unroll
-            for (int i = 0; i < kRb; ++i) acc[i] = T[(c0 + i) * kTileStride + tid];
-#pragma unroll 4
-            for (int j = 0; j < c0; ++j) trsm_axpy16(acc, T[j * kTileStride + tid], S + j * kStripStride + (c0 - s0));
+            for (int i = 0; i < kRb; i += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(Tr + c0 + i);
+                acc[i] = v.x;
+                acc[i + 1] = v.y;
+                acc[i + 2] = v.z;
+                acc[i + 3] = v.w;
+            }
+#pragma unroll 2
+            for (int j = 0; j < c0; j += 4)
+                trsm_axpy16x4(acc, *reinterpret_cast<const float4*>(Tr + j), S + j * sp + (c0 - s0), sp);
 #pragma unroll
             for (int jj = 0; jj < kRb; ++jj) {
                 if (c0 + jj < s1) {
-                    const float* Sj = S + (c0 + jj) * kStripStride + (c0 - s0);
+                    const float* Sj = S + (c0 + jj) * sp + (c0 - s0);
                     const float u = Sj[jj];
                     acc[jj] = (u != 0.f) ? acc[jj] / u : 0.f;
 #pragma unroll
@@ -149,61 +194,83 @@ __global__ void __launch_bounds__(kRowCta) trsm_l21_rows_kernel(float* __restric
                 }
             }
 #pragma unroll
-            for (int i = 0; i < kRb; ++i) T[(c0 + i) * kTileStride + tid] = acc[i];
+            for (int i = 0; i < kRb; i += 4)
+                *reinterpret_cast<float4*>(Tr + c0 + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
         }
     }
     __syncthreads();
-    for (int r = warp; r < nrow; r += kRowCta / 32)
-        for (int j = lane; j < w; j += 32) A[idx(r0 + r, k + j, lda)] = T[j * kTileStride + r];
+    for (int e = tid; e < nrow * w; e += kRowCta) {
+        const int r = e / w, j = e - r * w;
+        A[idx(r0 + r, k + j, lda)] = T[static_cast<size_t>(r) * tp + j];
+    }
 }
 
 // U12 = L00^{-1} * A12 (unit lower L00 = the strict lower part of the
-// diagonal block).  Thread c owns column c0 + c.  Per strip of kStrip rows
-// [s0, s1) the CTA stages L00[s0:s1, 0:s1) transposed, S[p][i - s0] =
-// L(i, p) for p < i (zeros elsewhere), then each thread takes its column's
-// register blocks of the strip: the updates of every earlier row p, then the
-// block's own rows in order.  Per element: fma over p ascending.
-__global__ void __launch_bounds__(kRowCta) trsm_u12_cols_kernel(float* __restrict__ A, int lda, int n, int k, int w) {
+// diagonal block).  Thread c owns column cb + c of the tile T[i][c].  Per
+// strip of kStrip rows [s0, s1) the CTA stages rows s0..s1-1 of L00
+// (columns 0..s1-1; only entries left of the diagonal are read), then each
+// thread takes its column's register blocks of the strip: the updates of
+// every earlier row p, four at a time (one 16-byte read of L per row of the
+// block), then the block's own rows in order.  Per element: fma over p
+// ascending.
+__global__ void __launch_bounds__(kRowCta) trsm_u12_cols_kernel(float* __restrict__ A, int lda, int n, int k, int w,
+                                                                int vec) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* S = reinterpret_cast<float*>(smem_raw);
-    float* T = S + static_cast<size_t>(w) * kStripStride;    // T[i][c], stride kTileStride
     const int wp = trsm_wp(w);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tp = trsm_pitch(kRowCta), sp = trsm_pitch(wp);
+    float* T = reinterpret_cast<float*>(smem_raw);
+    float* S = T + static_cast<size_t>(wp) * tp;
+    const int tid = threadIdx.x;
     const int cb = k + w + blockIdx.x * kRowCta;
     const int ncol = min(kRowCta, n - cb);
-    for (int i = warp; i < wp; i += kRowCta / 32)
-        for (int c = lane; c < kRowCta; c += 32)
-            T[i * kTileStride + c] = (i < w && c < ncol) ? A[idx(k + i, cb + c, lda)] : 0.f;
+    trsm_stage(T, tp, A + idx(k, cb, lda), lda, wp, kRowCta, w, ncol, vec != 0);
     for (int s0 = 0; s0 < w; s0 += kStrip) {
         const int s1 = min(s0 + kStrip, w);
         __syncthreads();
-        for (int e = tid; e < kStrip * s1; e += kRowCta) {
-            const int ii = e / s1, p = e - ii * s1;       // row s0 + ii of L00, coalesced along p
-            const int i = s0 + ii;
-            S[p * kStripStride + ii] = (i < s1 && p < i) ? A[idx(k + i, k + p, lda)] : 0.f;
-        }
+        trsm_stage(S, sp, A + idx(k + s0, k, lda), lda, kStrip, wp, s1 - s0, s1, vec != 0);
         __syncthreads();
         for (int i0 = s0; i0 < s1; i0 += kRb) {
+            const float* Sb = S + static_cast<size_t>(i0 - s0) * sp;   // row i0 of L00
             float acc[kRb];
 #pragma unroll
-            for (int i = 0; i < kRb; ++i) acc[i] = T[(i0 + i) * kTileStride + tid];
-#pragma unroll 4
-            for (int p = 0; p < i0; ++p) trsm_axpy16(acc, T[p * kTileStride + tid], S + p * kStripStride + (i0 - s0));
+            for (int i = 0; i < kRb; ++i) acc[i] = T[(i0 + i) * tp + tid];
+#pragma unroll 2
+            for (int p = 0; p < i0; p += 4) {
+                const float x0 = T[p * tp + tid], x1 = T[(p + 1) * tp + tid];
+                const float x2 = T[(p + 2) * tp + tid], x3 = T[(p + 3) * tp + tid];
 #pragma unroll
-            for (int pp = 0; pp + 1 < kRb; ++pp) {
-                if (i0 + pp < s1) {
-                    const float* Sp = S + (i0 + pp) * kStripStride + (i0 - s0);
-#pragma unroll
-                    for (int i = pp + 1; i < kRb; ++i) acc[i] = fmaf(-Sp[i], acc[pp], acc[i]);
+                for (int i = 0; i < kRb; ++i) {
+                    const float4 l = *reinterpret_cast<const float4*>(Sb + i * sp + p);
+                    acc[i] = fmaf(-l.x, x0, acc[i]);
+                    acc[i] = fmaf(-l.y, x1, acc[i]);
+                    acc[i] = fmaf(-l.z, x2, acc[i]);
+                    acc[i] = fmaf(-l.w, x3, acc[i]);
                 }
             }
 #pragma unroll
-            for (int i = 0; i < kRb; ++i) T[(i0 + i) * kTileStride + tid] = acc[i];
+            for (int pp = 0; pp + 1 < kRb; ++pp) {
+                if (i0 + pp < s1) {
+#pragma unroll
+                    for (int i = pp + 1; i < kRb; ++i) acc[i] = fmaf(-Sb[i * sp + i0 + pp], acc[pp], acc[i]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < kRb; ++i) T[(i0 + i) * tp + tid] = acc[i];
         }
     }
     __syncthreads();
-    for (int i = warp; i < w; i += kRowCta / 32)
-        for (int c = lane; c < ncol; c += 32) A[idx(k + i, cb + c, lda)] = T[i * kTileStride + c];
+    for (int i = threadIdx.x >> 5; i < w; i += kRowCta / 32)
+        for (int c = threadIdx.x & 31; c < ncol; c += 32) A[idx(k + i, cb + c, lda)] = T[i * tp + c];
+}
+
+// Panels wider than this much shared memory allows (w > 384) take the
+// four-threads-per-row kernels.
+constexpr size_t kTrsmSmemMax = 200 * 1024;
+
+// 16-byte asynchronous staging needs every staged row to start 16-byte
+// aligned: the base and the leading dimension in whole 16-byte chunks.
+inline int trsm_vec(const void* p, int ld) {
+    return ((reinterpret_cast<uintptr_t>(p) & 15) == 0 && (ld & 3) == 0) ? 1 : 0;
 }
 
 template <typename E>
@@ -211,11 +278,17 @@ int trsm_l21(E* A, int lda, int m, int k, int w, const E* U, int ldu, cudaStream
     const int rows = m - k - w;
     if (rows <= 0) return 0;
     ProfScope ps(LU_PROF_TRSM_L21, s, static_cast<double>(rows) * w * w);
+    bool done = false;
     if constexpr (sizeof(E) == 4) {
-        const size_t smem = trsm_rows_smem(w);
-        if (int rc_ = smem_attr(trsm_l21_rows_kernel, smem)) return rc_;
-        trsm_l21_rows_kernel<<<cdiv(rows, kRowCta), kRowCta, smem, s>>>(A, lda, m, k, w, U, ldu);
-    } else {
+        const size_t smem = trsm_l21_smem(w);
+        if (smem <= kTrsmSmemMax) {
+            if (int rc_ = smem_attr(trsm_l21_rows_kernel, smem)) return rc_;
+            const int vec = trsm_vec(A + idx(k + w, k, lda), lda) & trsm_vec(U, ldu);
+            trsm_l21_rows_kernel<<<cdiv(rows, kRowCta), kRowCta, smem, s>>>(A, lda, m, k, w, U, ldu, vec);
+            done = true;
+        }
+    }
+    if (!done) {
         const size_t smem = static_cast<size_t>(w) * kL21Stride * sizeof(E);
         if (int rc_ = smem_attr(trsm_l21_kernel<E>, smem)) return rc_;
         trsm_l21_kernel<E><<<cdiv(rows, kL21Rows), 256, smem, s>>>(A, lda, m, k, w, U, ldu);
@@ -230,11 +303,17 @@ int trsm_u12(E* A, int lda, int n, int k, int w, cudaStream_t s) {
     const int cols = n - k - w;
     if (cols <= 0 || w <= 1) return 0;
     ProfScope ps(LU_PROF_TRSM_U12, s, static_cast<double>(cols) * w * (w - 1));
+    bool done = false;
     if constexpr (sizeof(E) == 4) {
-        const size_t smem = trsm_rows_smem(w);
-        if (int rc_ = smem_attr(trsm_u12_cols_kernel, smem)) return rc_;
-        trsm_u12_cols_kernel<<<cdiv(cols, kRowCta), kRowCta, smem, s>>>(A, lda, n, k, w);
-    } else {
+        const size_t smem = trsm_u12_smem(w);
+        if (smem <= kTrsmSmemMax) {
+            if (int rc_ = smem_attr(trsm_u12_cols_kernel, smem)) return rc_;
+            const int vec = trsm_vec(A + idx(k, k + w, lda), lda) & trsm_vec(A + idx(k, k, lda), lda);
+            trsm_u12_cols_kernel<<<cdiv(cols, kRowCta), kRowCta, smem, s>>>(A, lda, n, k, w, vec);
+            done = true;
+        }
+    }
+    if (!done) {
         const size_t smem = static_cast<size_t>(w) * kU12Cols * sizeof(E);
         if (int rc_ = smem_attr(trsm_u12_kernel<E>, smem)) return rc_;
         trsm_u12_kernel<E><<<cdiv(cols, kU12Cols), 256, smem, s>>>(A, lda, n, k, w);
