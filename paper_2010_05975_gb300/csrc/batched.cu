@@ -85,7 +85,7 @@ __device__ void node_select(Smem<T>& sm, const T* A, int lda, int k, int w, int 
         W[r * ws + j] = A[idx(sm.ids[r], k + j, lda)];
     }
     __syncthreads();
-    node_gepp_blocked<T, false>(W, ws, nr, w, min(nr, w), sm.ids, sm.ord, out, sm.lrow, sm.gs,
+    node_gepp_blocked<T, false, 2>(W, ws, nr, w, min(nr, w), sm.ids, sm.ord, out, sm.lrow, sm.gs,
                          root ? &sm.zero_first : nullptr);
     if (root)
         for (int e = tid; e < nr * w; e += blockDim.x) {

@@ -141,59 +141,50 @@ __device__ __forceinline__ void gepp_bar(int id, int nthreads) {
 }
 
 // Row r of W: its trailing columns from j0 (rounded down to 16 bytes; the
-// columns before j0 are written back unchanged), chunks i = s, s+S, ...,
-// four in flight, each taking the panel's KB updates in pivot order.  Pivot
-// row q is row rq[q] of Ub (stride us).
-template <typename T, bool FULL>
+// columns before j0 and from w on are written back unchanged), chunks
+// i = s, s+S, ..., each taking the panel's KB updates in pivot order: QB
+// pivot rows' chunks are read at a time, then their fused multiply-adds.
+// Pivot row q is row rq[q] of Ub (stride us); without FULL, steps q >= kb
+// and steps whose pivot was zero (bit q of zm) are skipped.
+template <typename T, bool FULL, int QB = kGeppKB>
 __device__ __forceinline__ void gepp_rank_row(T* W, int ws, int r, int s, int S, int j0, int w,
                                               const T (&mr)[kGeppKB], const T* Ub, int us,
                                               const int (&rq)[kGeppKB], int kb, unsigned zm) {
     constexpr int KB = kGeppKB;
     constexpr int V = 16 / sizeof(T);
-    constexpr int NF = 4;                               // chunks in flight
+    static_assert(KB % QB == 0, "pivot groups must tile the panel");
     const int cb = j0 & ~(V - 1);
     const int nch = (w - cb + V - 1) / V;
     T* row = W + static_cast<size_t>(r) * ws;
-    for (int i = s; i < nch; i += NF * S) {
-        T a[NF][V], a0[NF][V];
-        int jj[NF];
-        bool has[NF];
+    for (int i = s; i < nch; i += S) {
+        const int j = cb + V * i;
+        T a[V], a0[V];
+        gepp_ld16(row + j, a);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            jj[f] = cb + V * (i + f * S);
-            has[f] = (i + f * S) < nch;
-            if (has[f]) {
-                gepp_ld16(row + jj[f], a[f]);
-            } else {
+        for (int v = 0; v < V; ++v) a0[v] = a[v];
 #pragma unroll
-                for (int v = 0; v < V; ++v) a[f][v] = T(0);
+        for (int q0 = 0; q0 < KB; q0 += QB) {
+            T u[QB][V];
+#pragma unroll
+            for (int t = 0; t < QB; ++t) {
+                const int q = q0 + t;
+                if (FULL || (q < kb && !((zm >> q) & 1u))) gepp_ld16(Ub + static_cast<size_t>(rq[q]) * us + j, u[t]);
             }
 #pragma unroll
-            for (int v = 0; v < V; ++v) a0[f][v] = a[f][v];
-        }
+            for (int t = 0; t < QB; ++t) {
+                const int q = q0 + t;
+                if (FULL || (q < kb && !((zm >> q) & 1u))) {
 #pragma unroll
-        for (int q = 0; q < KB; ++q) {
-            if (FULL || (q < kb && !((zm >> q) & 1u))) {
-                const T* up = Ub + static_cast<size_t>(rq[q]) * us;
-#pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    if (has[f]) {
-                        T u[V];
-                        gepp_ld16(up + jj[f], u);
-#pragma unroll
-                        for (int v = 0; v < V; ++v) a[f][v] = fma(-mr[q], u[v], a[f][v]);
-                    }
+                    for (int v = 0; v < V; ++v) a[v] = fma(-mr[q], u[t][v], a[v]);
                 }
             }
         }
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            if (!has[f]) continue;
+        if (j < j0 || j + V > w) {
 #pragma unroll
             for (int v = 0; v < V; ++v)
-                if (jj[f] + v < j0 || jj[f] + v >= w) a[f][v] = a0[f][v];
-            gepp_st16(row + jj[f], a[f]);
+                if (j + v < j0 || j + v >= w) a[v] = a0[v];
         }
+        gepp_st16(row + j, a);
     }
 }
 
@@ -212,7 +203,7 @@ __device__ __forceinline__ void gepp_rank_row(T* W, int ws, int r, int s, int S,
 // Requires nr <= blockDim.x (a multiple of 32) and ns <= min(nr, w).  The
 // caller has made W, ids and ord visible to the block (a barrier); the
 // function ends with a block barrier.  Named barrier 1 is used.
-template <typename T, bool LREG = (sizeof(T) == 4)>
+template <typename T, bool LREG = (sizeof(T) == 4), int QB = kGeppKB>
 __device__ void node_gepp_blocked(T* W, int ws, int nr, int w, int ns, const int* ids, int* ord, int* winp,
                                   int* lrow, GeppSlots<T>& sl, int* zero_first) {
     constexpr int KB = kGeppKB;
@@ -353,9 +344,9 @@ __device__ void node_gepp_blocked(T* W, int ws, int nr, int w, int ns, const int
             T mr[KB];
             gepp_vload(W + static_cast<size_t>(r) * ws + c0, mr);
             if (kb == KB && zm == 0)
-                gepp_rank_row<T, true>(W, ws, r, s, S, j0, w, mr, W, ws, rq, kb, zm);
+                gepp_rank_row<T, true, QB>(W, ws, r, s, S, j0, w, mr, W, ws, rq, kb, zm);
             else
-                gepp_rank_row<T, false>(W, ws, r, s, S, j0, w, mr, W, ws, rq, kb, zm);
+                gepp_rank_row<T, false, QB>(W, ws, r, s, S, j0, w, mr, W, ws, rq, kb, zm);
         }
         __syncthreads();
     }
