@@ -305,7 +305,11 @@ typedef struct {
     double tol;             /* stop when max_c eta_c <= tol (default 1e-12)    */
     int max_iter;           /* outer refinement steps (default 40)             */
     int gmres_restart;      /* FGMRES restart length (default 30, max 200)     */
-    int reserved[4];        /* must be zero                                     */
+    int krylov_products;    /* products A z inside FGMRES: 0 (default) binary32
+                               multiplies first, binary64 from the first cycle
+                               that cuts eta by less than 10x; 1 binary64
+                               only; 2 binary32 multiplies only               */
+    int reserved[3];        /* must be zero                                     */
 } ir_opts;
 
 typedef struct {
@@ -318,6 +322,8 @@ typedef struct {
     double eta0;            /* max_c eta_c of the first solve                   */
     int precision;          /* factorization precision in use at the end        */
     int refactors;          /* times the ladder moved up a precision            */
+    int cycles32;           /* FGMRES cycles run with binary32-multiply products */
+    int cycles64;           /* FGMRES cycles run with binary64 products          */
 } ir_result;
 
 /*
@@ -329,7 +335,12 @@ typedef struct {
  * returns when X is final.  Classical refinement (x += LU^{-1} r) runs while
  * each step cuts eta by 4x or more; after that the correction equation is
  * solved by right-preconditioned flexible GMRES (binary64 Arnoldi and
- * Gram-Schmidt, the fp32 LU solve as preconditioner).  When an FGMRES cycle
+ * Gram-Schmidt, the fp32 LU solve as preconditioner).  Its products A z
+ * first use binary32 multiplies (A and z rounded to binary32, 32-term
+ * binary32 runs summed in binary64) with an inner tolerance of 1e-6: the
+ * outer binary64 residual corrects what they miss.  Once such a cycle cuts
+ * eta by less than 10x (kappa too large for them) the products are
+ * binary64.  When a binary64 FGMRES cycle
  * gains less than 10x, or two cycles do not reach tol, the matrix is
  * refactored one precision up (fp8 -> bf16 -> fp32) and refinement goes on
  * from the current X.  max_iter bounds the refinement steps over all levels.
@@ -444,7 +455,8 @@ int serve_destroy(serve_t *h);
 #define LU_PROF_OTHER     8   /* conversions, copies, scaling                    */
 #define LU_PROF_CHOL_DIAG 9   /* Cholesky diagonal-block factorization           */
 #define LU_PROF_SYRK      10  /* Cholesky trailing update (lower triangle)       */
-#define LU_PROF_NCLASS    11
+#define LU_PROF_MATVEC32  11  /* Krylov products with binary32 multiplies        */
+#define LU_PROF_NCLASS    12
 
 typedef struct {
     int kernel_class;        /* LU_PROF_*                                        */

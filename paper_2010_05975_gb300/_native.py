@@ -40,13 +40,15 @@ class lu_opts(ctypes.Structure):
 
 class ir_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("b", ctypes.c_int), ("h", ctypes.c_int), ("tol", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("max_iter", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("krylov_products", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class ir_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("gmres_iters", ctypes.c_int), ("path", ctypes.c_int),
                 ("info", ctypes.c_int), ("eta", ctypes.c_double), ("eta0", ctypes.c_double),
-                ("precision", ctypes.c_int), ("refactors", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("refactors", ctypes.c_int), ("cycles32", ctypes.c_int),
+                ("cycles64", ctypes.c_int)]
 
 
 class serve_cfg(ctypes.Structure):
@@ -88,7 +90,7 @@ class lu_prof_entry(ctypes.Structure):
 
 
 PROF_CLASSES = ["tslu", "pivot", "trsm_l21", "trsm_u12", "schur_f64", "schur_lowp", "solve", "residual", "other",
-                "chol_diag", "syrk"]
+                "chol_diag", "syrk", "matvec32"]
 
 _lock = threading.Lock()
 _lib = None

@@ -25,6 +25,18 @@
 
 namespace lu {
 
+// 16-byte asynchronous copy global -> shared (cp.async); bytes < 16 reads
+// that many and zero-fills the rest (0: nothing is read).  Both addresses
+// 16-byte aligned.  cp_async_wait_all() waits for the thread's own copies.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most one committed group of the thread's copies is pending
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 // Raise a kernel's dynamic shared-memory cap to at least `bytes` (per kernel
 // and device; never lowered, so concurrent callers with different sizes on
 // other host threads cannot shrink it under each other).

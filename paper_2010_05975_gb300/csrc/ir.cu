@@ -10,7 +10,12 @@
 // Once a classical step cuts eta by less than 4x, the correction equation
 // A d = r is solved instead (for the rest of the solve) by
 // right-preconditioned flexible GMRES (binary64 Arnoldi, preconditioner =
-// the fp32 solve, classical Gram-Schmidt applied twice, restart m).
+// the fp32 solve, classical Gram-Schmidt applied twice, restart m).  The
+// Arnoldi products A z first use binary32 multiplies (matvec32_kernel): the
+// correction equation only has to be solved to a relative accuracy well
+// above binary32's, since the next binary64 residual measures and corrects
+// what the cycle missed; a cycle that cuts eta by less than 10x shows the
+// products too coarse for this matrix, and later cycles use binary64 ones.
 //
 // Multi-column blocks are n x nrhs row-major.  Reductions are two-pass with
 // fixed order, so results do not depend on scheduling.
@@ -84,6 +89,122 @@ __global__ void __launch_bounds__(256) residual_kernel(int n, int nrhs, const do
                     if (cc == c) s = acc[r][cc];
                 if (row < n && c < ng) R[idx(row, g0 + c, ldr)] = B ? B[idx(row, g0 + c, ldb)] - s : s;
             }
+        }
+    }
+}
+
+// W = A Z with binary32 multiplies, for the Krylov products: A's entries and
+// Z's are rounded to binary32 and multiplied-added in binary32 over runs of
+// kMv32Chunk / 32 terms per lane, each run's sum added into a binary64
+// accumulator; the lanes' sums are combined in binary64.  Zf holds one group
+// of up to kMv32RG columns of Z in binary32, row-major with stride kMv32RG
+// (zf_kernel); A is read once per group.  One warp per kMv32RowsW rows, 16
+// warps per CTA.  Zf's chunks of kMv32Chunk rows arrive in shared memory by
+// 16-byte asynchronous copies, two buffers so that the next chunk lands
+// while the current one is used (row pitch kMv32Pitch: each lane's 16-byte
+// reads of its own row hit distinct bank groups).
+constexpr int kMv32RG = 16;
+constexpr int kMv32RowsW = 2;
+constexpr int kMv32Threads = 512;
+constexpr int kMv32Rows = (kMv32Threads / 32) * kMv32RowsW;   // rows per CTA
+constexpr int kMv32Pitch = kMv32RG + 4;
+constexpr int kMv32Chunk = 1024;
+constexpr size_t kMv32Smem = 2 * static_cast<size_t>(kMv32Chunk) * kMv32Pitch * sizeof(float);
+
+// Zf[j][c] = (float) Z[j][g0 + c] for c < ng, 0 for ng <= c < kMv32RG.
+__global__ void zf_kernel(int n, int g0, int ng, const double* __restrict__ Z, int ldz, float* __restrict__ Zf) {
+    const long long tot = static_cast<long long>(n) * kMv32RG;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < tot;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int j = static_cast<int>(e / kMv32RG), c = static_cast<int>(e % kMv32RG);
+        Zf[e] = c < ng ? __double2float_rn(Z[idx(j, g0 + c, ldz)]) : 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(kMv32Threads, 1) matvec32_kernel(int n, int g0, int ng, const double* __restrict__ A,
+                                                                   int lda, const float* __restrict__ Zf,
+                                                                   double* __restrict__ W, int ldw) {
+    extern __shared__ __align__(16) float zs[];         // [2][kMv32Chunk][kMv32Pitch]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int row0 = blockIdx.x * kMv32Rows + warp * kMv32RowsW;
+    const double* arow[kMv32RowsW];
+#pragma unroll
+    for (int r = 0; r < kMv32RowsW; ++r) arow[r] = A + idx(min(row0 + r, n - 1), 0, lda);
+    const int nchunk = (n + kMv32Chunk - 1) / kMv32Chunk;
+    // chunk k -> buffer k & 1: rows j0 .. j0 + nj of Zf, 4 x 16 bytes each
+    auto stage = [&](int k) {
+        const int j0 = k * kMv32Chunk, nj = min(kMv32Chunk, n - j0);
+        float* dst = zs + (k & 1) * kMv32Chunk * kMv32Pitch;
+        for (int e = threadIdx.x; e < nj * (kMv32RG / 4); e += kMv32Threads) {
+            const int jj = e / (kMv32RG / 4), q = e % (kMv32RG / 4);
+            cp_async16(dst + jj * kMv32Pitch + 4 * q, Zf + static_cast<size_t>(j0 + jj) * kMv32RG + 4 * q, 16);
+        }
+        cp_async_commit();
+    };
+    double acc[kMv32RowsW][kMv32RG];
+#pragma unroll
+    for (int r = 0; r < kMv32RowsW; ++r)
+#pragma unroll
+        for (int c = 0; c < kMv32RG; ++c) acc[r][c] = 0.0;
+    stage(0);
+    for (int k = 0; k < nchunk; ++k) {
+        if (k + 1 < nchunk) {
+            stage(k + 1);
+            cp_async_wait_1();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();                                 // chunk k is in for every thread
+        const int j0 = k * kMv32Chunk, nj = min(kMv32Chunk, n - j0);
+        const float* zb = zs + (k & 1) * kMv32Chunk * kMv32Pitch;
+        float run[kMv32RowsW][kMv32RG];
+#pragma unroll
+        for (int r = 0; r < kMv32RowsW; ++r)
+#pragma unroll
+            for (int c = 0; c < kMv32RG; ++c) run[r][c] = 0.f;
+#pragma unroll 4
+        for (int jj = lane; jj < nj; jj += 32) {
+            float a[kMv32RowsW];
+#pragma unroll
+            for (int r = 0; r < kMv32RowsW; ++r) a[r] = __double2float_rn(arow[r][j0 + jj]);
+            const float* zr = zb + jj * kMv32Pitch;
+#pragma unroll
+            for (int c = 0; c < kMv32RG; c += 4) {
+                const float4 z4 = *reinterpret_cast<const float4*>(zr + c);
+#pragma unroll
+                for (int r = 0; r < kMv32RowsW; ++r) {
+                    run[r][c] = fmaf(a[r], z4.x, run[r][c]);
+                    run[r][c + 1] = fmaf(a[r], z4.y, run[r][c + 1]);
+                    run[r][c + 2] = fmaf(a[r], z4.z, run[r][c + 2]);
+                    run[r][c + 3] = fmaf(a[r], z4.w, run[r][c + 3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kMv32RowsW; ++r)
+#pragma unroll
+            for (int c = 0; c < kMv32RG; ++c) acc[r][c] += static_cast<double>(run[r][c]);
+        __syncthreads();                                 // buffer k & 1 is free for chunk k + 2
+    }
+#pragma unroll
+    for (int r = 0; r < kMv32RowsW; ++r)
+#pragma unroll
+        for (int c = 0; c < kMv32RG; ++c) {
+            double v = acc[r][c];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            acc[r][c] = v;
+        }
+    if (lane < kMv32RG) {
+        const int c = lane;
+#pragma unroll
+        for (int r = 0; r < kMv32RowsW; ++r) {
+            const int row = row0 + r;
+            double v = 0.0;
+#pragma unroll
+            for (int cc = 0; cc < kMv32RG; ++cc)
+                if (cc == c) v = acc[r][cc];
+            if (row < n && c < ng) W[idx(row, g0 + c, ldw)] = v;
         }
     }
 }
@@ -268,6 +389,24 @@ int residual_f64(int n, int nrhs, const double* A, int lda, const double* X, int
     return 0;
 }
 
+// W = A Z with binary32 multiplies (the Krylov products; see matvec32_kernel).
+// zf: scratch of n x kMv32RG floats, 16-byte aligned.
+int matvec32(int n, int nrhs, const double* A, int lda, const double* Z, int ldz, double* W, int ldw, float* zf,
+             cudaStream_t s) {
+    if (n == 0 || nrhs == 0) return 0;
+    ProfScope ps(LU_PROF_MATVEC32, s, 2.0 * n * static_cast<double>(n) * nrhs,
+                 8.0 * static_cast<double>(n) * n * cdiv(nrhs, kMv32RG));
+    if (int rc_ = smem_attr(matvec32_kernel, kMv32Smem)) return rc_;
+    for (int g0 = 0; g0 < nrhs; g0 += kMv32RG) {
+        const int ng = nrhs - g0 < kMv32RG ? nrhs - g0 : kMv32RG;
+        zf_kernel<<<grid_for(static_cast<long long>(n) * kMv32RG), 256, 0, s>>>(n, g0, ng, Z, ldz, zf);
+        matvec32_kernel<<<cdiv(n, kMv32Rows), kMv32Threads, kMv32Smem, s>>>(n, g0, ng, A, lda, zf, W, ldw);
+        count_launches(2);
+    }
+    LU_LAUNCHED();
+    return 0;
+}
+
 static int col_reduce(int n, int nrhs, const double* X, int ldx, const double* Y, int ldy, int op, double* part,
                       double* out, cudaStream_t s) {
     ProfScope ps(LU_PROF_RESIDUAL, s);
@@ -377,6 +516,7 @@ struct IrCtx {
     const SolvePlan<float>* plan;   // their solve plan
     double* R;        // n x nrhs
     float* r32;       // n x nrhs
+    float* zf;        // n x 16: binary32 copy of a Krylov vector (matvec32)
     double* part;     // reduction partials
     double* vec;      // small per-column vectors: [0] scale, [nrhs] eta, ...
     double* an;
@@ -426,7 +566,8 @@ int backward_error(IrCtx& c, double* eta_h, double* bmax_d) {
 
 // One restart cycle of right-preconditioned flexible GMRES on A d = R for
 // every column at once; X += d.  Returns the inner iterations done.
-int fgmres_cycle(IrCtx& c, int m, double gtol, double* V, double* Z, double* W, double* H, int* iters_out) {
+int fgmres_cycle(IrCtx& c, int m, double gtol, bool mv32, double* V, double* Z, double* W, double* H,
+                 int* iters_out) {
     const int n = c.n, nr = c.nrhs;
     const size_t vs = static_cast<size_t>(n) * nr;
     double* scale = c.vec;
@@ -455,7 +596,9 @@ int fgmres_cycle(IrCtx& c, int m, double gtol, double* V, double* Z, double* W, 
         double* Vj = V + j * vs;
         double* Zj = Z + j * vs;
         if (int rc = precond_apply(c, Vj, Zj, scale)) return rc;
-        if (int rc = residual_f64(n, nr, c.A, c.lda, Zj, nr, nullptr, 0, W, nr, c.s)) return rc;   // W = A z
+        if (int rc = mv32 ? matvec32(n, nr, c.A, c.lda, Zj, nr, W, nr, c.zf, c.s)                  // W = A z
+                          : residual_f64(n, nr, c.A, c.lda, Zj, nr, nullptr, 0, W, nr, c.s))
+            return rc;
         // classical Gram-Schmidt, twice
         for (int pass = 0; pass < 2; ++pass) {
             {
@@ -618,6 +761,7 @@ int ir_refine(IrFactors* fac, const double* A, int lda, int nrhs, const double* 
     const size_t vs = static_cast<size_t>(n) * nrhs;
     c.R = dev.alloc<double>(vs);
     c.r32 = dev.alloc<float>(vs);
+    c.zf = dev.alloc<float>(static_cast<size_t>(n) * kMv32RG);
     const size_t part_words = static_cast<size_t>(kRedBlocks) * nrhs * 4 + static_cast<size_t>(restart + 2) * 16 * nrhs;
     c.part = dev.alloc<double>(part_words);
     c.vec = dev.alloc<double>(8 * static_cast<size_t>(nrhs) + 8);
@@ -653,12 +797,16 @@ int ir_refine(IrFactors* fac, const double* A, int lda, int nrhs, const double* 
     // the current X.
     std::vector<double> eta(nrhs);
     int total_it = 0;
+    // Krylov products: binary32 multiplies until a cycle with them gains
+    // less than 10x (then binary64 for the rest of the solve)
+    bool mv32 = opt.krylov_products != 1;
     for (;;) {
         const bool last = (fac->precision == LU_PREC_F32);
         double prev = 0.0;
         bool krylov = false;
         int cycles = 0;
         bool escalate = false;
+        bool last_mv32 = false;      // the cycle just run used binary32 multiplies
         for (;;) {
             if (int rc = backward_error(c, eta.data(), bmax)) return rc;
             double em = 0.0;
@@ -672,9 +820,16 @@ int ir_refine(IrFactors* fac, const double* A, int lda, int nrhs, const double* 
                 return 0;
             }
             if (total_it >= max_iter) return 0;
-            // stall tests: a Krylov cycle that gains less than 10x, or two
-            // cycles without reaching tol, move up the ladder
-            if (krylov && !last && (cycles >= 2 || em > 0.1 * prev)) {
+            // a binary32-product cycle that gained less than 10x: binary64
+            // products from now on; that cycle does not count below
+            if (last_mv32 && opt.krylov_products == 0 && em > 0.1 * prev) {
+                mv32 = false;
+                cycles = 0;
+            }
+            // stall tests: a binary64-product cycle that gains less than 10x,
+            // or two of them without reaching tol, move up the ladder
+            const bool counted = !last_mv32 || opt.krylov_products == 2;
+            if (krylov && counted && !last && (cycles >= 2 || em > 0.1 * prev)) {
                 escalate = true;
                 break;
             }
@@ -704,9 +859,16 @@ int ir_refine(IrFactors* fac, const double* A, int lda, int nrhs, const double* 
                     if (!dev.ok) return LU_ENOMEM;
                 }
                 int inner = 0;
-                if (int rc = fgmres_cycle(c, restart, 1e-10, V, Z, W, H, &inner)) return rc;
+                // binary32 products: the cycle's inner tolerance stops well above
+                // their accuracy; binary64: the usual 1e-10
+                if (int rc = fgmres_cycle(c, restart, mv32 ? 1e-6 : 1e-10, mv32, V, Z, W, H, &inner)) return rc;
                 res->gmres_iters += inner;
-                ++cycles;
+                last_mv32 = mv32;
+                if (mv32)
+                    res->cycles32 += 1;
+                else
+                    res->cycles64 += 1;
+                if (!mv32 || opt.krylov_products == 2) ++cycles;
             }
         }
         if (!escalate) return 0;
@@ -722,7 +884,7 @@ int ir_refine(IrFactors* fac, const double* A, int lda, int nrhs, const double* 
 size_t ir_workspace_bytes(int n, int nrhs, int restart) {
     const size_t vs = static_cast<size_t>(n) * nrhs;
     if (restart <= 0) restart = 30;
-    return vs * (8 + 4 + 8 * (2 * static_cast<size_t>(restart) + 2)) +
+    return vs * (8 + 4 + 8 * (2 * static_cast<size_t>(restart) + 2)) + static_cast<size_t>(n) * kMv32RG * 4 +
            (static_cast<size_t>(kRedBlocks) * nrhs * 4 + static_cast<size_t>(restart + 2) * 16 * nrhs + 16 * nrhs) * 8 +
            4096;
 }
@@ -742,6 +904,7 @@ extern "C" int ir_solve(int n, int nrhs, const double* A, int lda, const double*
     if (o) opt = *o;
     const int prec = opt.precision ? opt.precision : LU_PREC_BF16;
     if (prec < LU_PREC_F64 || prec > LU_PREC_FP8) return -9;
+    if (opt.krylov_products < 0 || opt.krylov_products > 2) return -11;
     *res = ir_result{};
     res->path = -1;
     if (n == 0 || nrhs == 0) {

@@ -97,14 +97,6 @@ inline size_t trsm_u12_smem(int w) {
             static_cast<size_t>(kStrip) * trsm_pitch(trsm_wp(w))) * sizeof(float);
 }
 
-// 16-byte asynchronous copy global -> shared; bytes < 16 reads that many
-// and zero-fills the rest (0: nothing is read).
-__device__ __forceinline__ void cp_async16(float* dst, const float* src, int bytes) {
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // Stage rows x cols of a row-major global block (leading dimension ld) into
 // shared memory (pitch floats per row), zero outside [0, vrows) x [0, vcols).
 // vec: the global rows start 16-byte aligned, so 16-byte asynchronous copies

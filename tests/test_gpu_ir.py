@@ -69,3 +69,35 @@ def test_residual_kernel(oracle_mod, n, nrhs):
     assert np.abs(R.cpu().numpy() - Rr).max() <= 4 * n * 2.0 ** -53 * scale
     eo = oracle_mod.backward_error(A, B, X)
     np.testing.assert_allclose(eta.cpu().numpy(), eo, rtol=1e-12)
+
+
+@pytest.mark.parametrize("prec,kappa", [(FP8, 1e2), (BF16, 1e4), (BF16, 1e6)])
+@pytest.mark.parametrize("products", [0, 1, 2])
+def test_ir_krylov_products(oracle_mod, prec, kappa, products):
+    """Every choice of Krylov products reaches 1e-12: binary32 multiplies
+    (2), binary64 (1), or the adaptive rule (0), which runs its first FGMRES
+    cycle with binary32 multiplies and stays with them while they pay."""
+    torch = cuda_or_fail()
+    g = lib()
+    n, nrhs = 1024, 8
+    A, B, Xt = make_problem(n, kappa, nrhs, seed=40 + int(np.log10(kappa)))
+    X, res = g.ir_solve(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), precision=prec,
+                        krylov_products=products)
+    eta = oracle_mod.backward_error(A, B, X.cpu().numpy())
+    assert res["eta"] <= 1e-12 and eta.max() <= 1e-12, (res, eta.max())
+    if res["path"] == 1:
+        if products == 1:
+            assert res["cycles32"] == 0 and res["cycles64"] >= 1, res
+        else:
+            assert res["cycles32"] >= 1, res
+        if products == 2:
+            assert res["cycles64"] == 0, res
+
+
+def test_ir_rejects_bad_krylov_option():
+    torch = cuda_or_fail()
+    g = lib()
+    from paper_2010_05975_gb300 import _native as nat
+    A = torch.eye(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(nat.LuError):
+        g.ir_solve(A, torch.ones(8, 1, dtype=torch.float64, device="cuda"), krylov_products=3)
