@@ -151,7 +151,8 @@ struct SolvePlan {
     const T* LU = nullptr;
     int lda = 0;
     int* perm = nullptr;
-    T* DT = nullptr;
+    T* DT = nullptr;           // inverses of the diagonal blocks, [block][L, U][NB][NB] row-major
+    T* M = nullptr;            // coupling blocks inv(L_bb) L_{b,b-1} / inv(U_bb) U_{b,b+1}, same layout
     int* off = nullptr;        // work items before each block step
     int chol = 0;              // LU is a Cholesky factor L: U = L^T, no permutation
 };

@@ -5,25 +5,35 @@
 //
 // A solve plan holds what depends on the factors only: the row permutation
 // composed from the swap sequence piv, and the inverses of the NB x NB
-// diagonal blocks of L (unit lower) and U (upper), stored transposed.  The
+// diagonal blocks of L (unit lower) and U (upper), and the coupling blocks
+// inv(L_bb) L_{b,b-1} and inv(U_bb) U_{b,b+1}, all stored row-major.  The
 // refinement keeps one plan per factorization; the one-shot entry points
 // build and drop one per call.
 //
 // Applying a plan: B is gathered through the permutation into Y (row stride
 // nc, padded to a width of 8, 16, 32 or 64), then one kernel runs the
 // blocked forward and backward substitutions as a list of work items taken
-// in order from an atomic counter.  Every item is a 32-row contraction:
-//   forward step b:   parts of X_b = inv(L_bb) Y_b (32 rows each), then for
-//                     every 32-row tile t below the block: Y_t -= L_tb X_b;
-//   backward step b:  (b from the last block up) the parts of
-//                     X_b = inv(U_bb) X_b, then the tiles above:
-//                     X_t -= U_tb X_b.
-// An item first stages its coefficient rows, then waits (bounded, through
-// per-tile and per-block counters) on items earlier in the list, which CTAs
-// already running have taken, so the kernel progresses whatever number of
-// its CTAs is resident.  Each tile takes its updates one step at a time, in
-// step order, so results do not depend on timing.  Right-hand sides go
-// through in passes of up to 64.
+// in order from an atomic counter.  Per block b the list holds
+//   the chain item  forward:  X_b = inv(L_bb) Y_b - M_b X_{b-1} with the
+//                   plan's coupling block M_b = inv(L_bb) L_{b,b-1};
+//                   backward: Y_b = inv(U_bb) X_b - M'_b Y_{b+1}, M'_b =
+//                   inv(U_bb) U_{b,b+1} (b from the last block up).  The
+//                   first product needs only the block's earlier updates, so
+//                   it runs before the previous chain item is done: one
+//                   product per step on the critical path.  It sits in the list
+//                   right after the block items of two steps back, a step
+//                   ahead of the bulk (solve_offsets_kernel);
+//   block items     forward:  for every block t two or more blocks below:
+//                   Y_t -= L_tb X_b;  backward: two or more blocks above:
+//                   X_t -= U_tb Y_b.
+// An item first stages its coefficient blocks (16-byte asynchronous copies
+// where the rows are aligned), then waits (bounded, through per-block
+// counters) on items earlier in the list, which CTAs already running have
+// taken, so the kernel progresses whatever number of its CTAs is resident.
+// Each block takes its updates one step at a time, in step order, each as
+// y - sum_p l_p x_p with the sum in p order, and every product has a fixed
+// order, so results do not depend on timing.  Right-hand sides go through in
+// passes of up to 64.
 #include "common.cuh"
 #include "prof.cuh"
 #include <mutex>
@@ -66,7 +76,7 @@ struct SolveNB {
     static constexpr int value = sizeof(T) == 4 ? 128 : 64;
 };
 
-// One CTA per (block, factor): Dinv[blk][kind] = inv(diag block).  Thread c
+// One CTA per (block, factor): Dinv[blk][kind] = inv(diag block), row-major.  Thread c
 // owns column c of the inverse; the block stays in shared memory.  With
 // chol set the factors are L (non-unit lower, from a Cholesky factorization)
 // and L^T: both kinds compute inv(L_bb), kind 1 stores inv(L_bb^T) =
@@ -120,19 +130,56 @@ __global__ void __launch_bounds__(128) invert_diag_kernel(int n, const T* __rest
         }
     }
     __syncthreads();
-    // transposed: out[p][i] = inv[i][p], so that a warp reads consecutive i
+    // row-major: out[i][p] = inv[i][p] (rows arrive in the solve by 16-byte copies)
     T* out = Dinv + (static_cast<size_t>(blk) * 2 + kind) * NB * NB;
     if (chol && kind == 1) {
-        // out[p][i] = inv(L^T)[i][p] = inv(L)[p][i]
-        for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) out[e] = Xs[(e / NB) * (NB + 1) + (e % NB)];
-    } else {
+        // out[i][p] = inv(L^T)[i][p] = inv(L)[p][i]
         for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) out[e] = Xs[(e % NB) * (NB + 1) + (e / NB)];
+    } else {
+        for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) out[e] = Xs[(e / NB) * (NB + 1) + (e % NB)];
+    }
+}
+
+// One CTA per (block, factor): M[blk][kind] = inv(diag block) times the
+// off-diagonal block next to it on the substitution's path (kind 0: L_{b,b-1},
+// kind 1: U_{b,b+1}; a Cholesky factor's U_{b,b+1} is L_{b+1,b}^T), row-major,
+// zero where it has no neighbour.  Fixed summation order.
+template <typename T>
+__global__ void __launch_bounds__(256) couple_kernel(int n, const T* __restrict__ LU, int lda,
+                                                     const T* __restrict__ Dinv, T* __restrict__ M, int chol) {
+    constexpr int NB = SolveNB<T>::value;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Ds = reinterpret_cast<T*>(smem_raw);              // NB x (NB+1)
+    T* Gs = Ds + NB * (NB + 1);                          // NB x (NB+1): the off-diagonal block
+    const int blk = blockIdx.x, kind = blockIdx.y;
+    const int nblk = cdiv(n, NB);
+    const int r0 = blk * NB, nb = min(NB, n - r0);
+    const int nbk = kind == 0 ? blk - 1 : blk + 1;
+    T* out = M + (static_cast<size_t>(blk) * 2 + kind) * NB * NB;
+    if (nbk < 0 || nbk >= nblk) {
+        for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) out[e] = T(0);
+        return;
+    }
+    const int c0 = nbk * NB, nc = min(NB, n - c0);
+    const T* D = Dinv + (static_cast<size_t>(blk) * 2 + kind) * NB * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int i = e / NB, j = e % NB;
+        Ds[i * (NB + 1) + j] = D[e];
+        T g = T(0);
+        if (i < nb && j < nc) g = (chol && kind == 1) ? LU[idx(c0 + j, r0 + i, lda)] : LU[idx(r0 + i, c0 + j, lda)];
+        Gs[i * (NB + 1) + j] = g;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int i = e / NB, j = e % NB;
+        T acc = T(0);
+        for (int q = 0; q < nb; ++q) acc = fma(Ds[i * (NB + 1) + q], Gs[q * (NB + 1) + j], acc);
+        out[e] = acc;
     }
 }
 
 constexpr int kSolveRhs = 64;            // right-hand sides per pass
-constexpr int kSolveTile = 32;           // rows per update tile
-constexpr int kSolveThreads = 256;
+constexpr int kSolveThreads = 512;
 
 // Item list bookkeeping (device memory, zeroed before each pass).
 struct SolveSync {
@@ -141,26 +188,26 @@ struct SolveSync {
     int pad[2];
 };
 
-// Items before forward step b / backward step b: off[0..2*nblk], built once
-// per plan (the block size arrives in off[0]).
+// Item groups: off[g] = first item of group g, g < 2 nblk, off[2 nblk] =
+// total; built once per plan (the block size arrives in off[0]).  Forward
+// group 0 = {C(0)}, group 1 = {C(1)}, group g >= 2 = {T(g-2, t) for blocks
+// t = g .. nblk-1, then C(g)}: the chain item of block g follows the block
+// items of step g-2, so it is taken (and stages its coefficients) a step
+// ahead of the bulk of step g-1.  Backward groups mirror it from the last
+// block: group g holds C'(nblk-1-g) after T'(nblk+1-g, t) for t = nblk-1-g
+// down to 0.
 __global__ void solve_offsets_kernel(int n, int* __restrict__ off) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    constexpr int TR = kSolveTile;
-    const int ntile = cdiv(n, TR);
     const int NB = off[0];
     const int nblk = cdiv(n, NB);
-    const int tpb = NB / TR;
     int acc = 0;
-    for (int b = 0; b < nblk; ++b) {                    // forward
-        off[b] = acc;
-        const int parts = cdiv(min(NB, n - b * NB), TR);
-        acc += parts + ntile - min(ntile, (b + 1) * tpb);
+    for (int g = 0; g < nblk; ++g) {                    // forward
+        off[g] = acc;
+        acc += g < 2 ? 1 : nblk - g + 1;
     }
-    for (int st = 0; st < nblk; ++st) {                 // backward, last block first
-        const int b = nblk - 1 - st;
-        off[nblk + st] = acc;
-        const int parts = cdiv(min(NB, n - b * NB), TR);
-        acc += parts + b * tpb;
+    for (int g = 0; g < nblk; ++g) {                    // backward: block b = nblk - 1 - g
+        off[nblk + g] = acc;
+        acc += g < 2 ? 1 : nblk - g + 1;
     }
     off[2 * nblk] = acc;
 }
@@ -189,32 +236,146 @@ __device__ __forceinline__ void solve_wait(const int* flag, int want, SolveSync*
     }
 }
 
+// Stage rows x cols of a row-major block (leading dimension ld) into shared
+// memory with row pitch cp, zero outside [0, vrows) x [0, vcols): 16-byte
+// asynchronous copies when vec (every staged row 16-byte aligned; cp a
+// multiple of 16 bytes), else plain loads.  The caller waits and syncs.
+template <typename T>
+__device__ __forceinline__ void solve_stage(T* dst, int cp, const T* src, size_t ld, int rows, int cols, int vrows,
+                                            int vcols, bool vec) {
+    constexpr int V = 16 / static_cast<int>(sizeof(T));
+    if (vec) {
+        const int cq = cols / V;
+        for (int e = threadIdx.x; e < rows * cq; e += kSolveThreads) {
+            const int r = e / cq, c = V * (e - r * cq);
+            const int bytes = (r < vrows) ? static_cast<int>(sizeof(T)) * max(0, min(V, vcols - c)) : 0;
+            cp_async16(dst + static_cast<size_t>(r) * cp + c, bytes ? src + r * ld + c : src, bytes);
+        }
+    } else {
+        for (int e = threadIdx.x; e < rows * cols; e += kSolveThreads) {
+            const int r = e / cols, c = e - r * cols;
+            dst[static_cast<size_t>(r) * cp + c] = (r < vrows && c < vcols) ? src[r * ld + c] : T(0);
+        }
+    }
+}
+
+// The transposed block (a Cholesky factor's U = L^T): dst[i][p] = src[p][i].
+template <typename T>
+__device__ __forceinline__ void solve_stage_t(T* dst, int cp, const T* src, size_t ld, int rows, int cols) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int p = warp; p < cols; p += kSolveThreads / 32)
+        for (int i = lane; i < rows; i += 32) dst[static_cast<size_t>(i) * cp + p] = src[p * ld + i];
+}
+
+// out[i][c] (op) = sum_{p < np} C[i][p] * Bm[p][c] for rows i < nr, p in
+// order.  A thread sums a 4 x 4 tile (rows 4 rg.., columns 4 cg..): per four
+// p it reads four 16-byte pieces of C rows and four of Bm rows for 64
+// multiply-adds, the ratio that keeps the shared-memory reads (their bytes
+// into registers, not the multiply-adds, bound these small products) low.
+// C row pitch cp and Bm row pitch NCW give 16-byte aligned rows.  sub: out =
+// base - sum; else out = sum.
+template <typename T>
+__device__ __forceinline__ void solve_ld4(const T* p, T (&v)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 x = *reinterpret_cast<const float4*>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
+    } else {
+        const double2 x = *reinterpret_cast<const double2*>(p);
+        const double2 y = *reinterpret_cast<const double2*>(p + 2);
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = y.x;
+        v[3] = y.y;
+    }
+}
+
+template <typename T, int NCW>
+__device__ __forceinline__ void solve_rows(const T* C, int cp, const T* Bm, int nr, int np, const T* base, int bstride,
+                                           T* out, int ostride, bool sub) {
+    constexpr int NB = SolveNB<T>::value;
+    constexpr int RB = 4;                              // rows per thread
+    constexpr int CG = NCW / 4;                        // column groups of four
+    constexpr int NT = (NB / RB) * CG;                 // threads in use
+    static_assert(NT <= kSolveThreads, "one thread per (row group, column group)");
+    if (threadIdx.x >= NT) return;
+    const int cg = threadIdx.x % CG, rg = threadIdx.x / CG;
+    const int i0 = rg * RB, c = 4 * cg;
+    if (i0 >= nr) return;
+    T acc[RB][4];
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[r][k] = T(0);
+    const T* Cr = C + static_cast<size_t>(i0) * cp;
+    const int np4 = np & ~3;
+    for (int p = 0; p < np4; p += 4) {
+        T cv[RB][4];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) solve_ld4(Cr + r * cp + p, cv[r]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            T bv[4];
+            solve_ld4(Bm + (p + q) * NCW + c, bv);
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[r][k] = fma(cv[r][q], bv[k], acc[r][k]);
+        }
+    }
+    for (int p = np4; p < np; ++p) {
+        T bv[4];
+        solve_ld4(Bm + p * NCW + c, bv);
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[r][k] = fma(Cr[r * cp + p], bv[k], acc[r][k]);
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        if (i0 + r >= nr) break;
+        const size_t i = static_cast<size_t>(i0 + r);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[i * ostride + c + k] = sub ? base[i * bstride + c + k] - acc[r][k] : acc[r][k];
+    }
+}
+
+// Coefficient row pitch: a whole number of 16-byte chunks plus one.
+template <typename T>
+__host__ __device__ constexpr int solve_cp() {
+    return SolveNB<T>::value + 16 / static_cast<int>(sizeof(T));
+}
+
 // Forward (L: Y -> X) then backward (U: X -> Y) substitution; right-hand
 // sides row-major with stride NCW (columns >= nc are zero and stay zero).
-// With chol set, U is L^T: the backward tiles read L transposed.
+// With chol set, U is L^T: the backward coefficients read L transposed.
+// xpf[b] / xpb[b]: the chain item of block b is done; fdone[t] / bdone[t]:
+// block items applied to block t.  vec: LU's rows are 16-byte aligned.
 template <typename T, int NCW>
 __global__ void __launch_bounds__(kSolveThreads) solve_items_kernel(int n, const T* __restrict__ LU, int lda,
-                                                                    const T* __restrict__ DT,
+                                                                    const T* __restrict__ DM,
+                                                                    const T* __restrict__ MM,
                                                                     const int* __restrict__ off, T* Y, T* X,
                                                                     int* fdone, int* bdone, int* xpf, int* xpb,
-                                                                    SolveSync* sy, int chol,
+                                                                    SolveSync* sy, int chol, int vec,
                                                                     unsigned long long wait_ns, int inject) {
     constexpr int NB = SolveNB<T>::value;
-    constexpr int TR = kSolveTile;
-    constexpr int TPB = NB / TR;                     // tiles (and solve parts) per block
-    constexpr int MU = NCW / 8;                      // columns per thread
+    constexpr int CP = solve_cp<T>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* Ls = reinterpret_cast<T*>(smem_raw);          // TR x (NB+1): the item's coefficient rows
-    T* Bs = Ls + TR * (NB + 1);                      // NB x NCW: the right operand
-    __shared__ int s_item, s_ph, s_b, s_t, s_q;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = kSolveThreads / 32;
-    const int nblk = cdiv(n, NB), ntile = cdiv(n, TR);
+    T* Cs = reinterpret_cast<T*>(smem_raw);          // NB x CP: off-diagonal coefficients
+    T* Ds = Cs + NB * CP;                            // NB x CP: inverse of the diagonal block (chain)
+    T* Bs = Ds + NB * CP;                            // NB x NCW: the neighbour's solution
+    T* Ws = Bs + NB * NCW;                           // NB x NCW: the block's current values
+    __shared__ int s_item, s_ph, s_b, s_t;
+    const int tid = threadIdx.x;
+    const int nblk = cdiv(n, NB);
     const int total = off[2 * nblk];
-    int bs_key = -1;                                 // which block Bs holds: (ph * 2 + kind) * nblk + b
     for (;;) {
         if (tid == 0) {
             const int item = atomicAdd(&sy->next, 1);
-            int ph = 0, b = 0, t = -1, q = 0;
+            int ph = 0, b = 0, t = -1;
             if (item < total) {
                 int lo = 0, hi = 2 * nblk - 1;
                 while (lo < hi) {
@@ -222,93 +383,94 @@ __global__ void __launch_bounds__(kSolveThreads) solve_items_kernel(int n, const
                     if (off[mid] <= item) lo = mid; else hi = mid - 1;
                 }
                 const int k = item - off[lo];
+                const int g = lo < nblk ? lo : lo - nblk;     // group within the phase
+                const int nbi = g < 2 ? 0 : nblk - g;          // block items before the chain item
                 ph = lo < nblk ? 0 : 1;
-                b = ph == 0 ? lo : nblk - 1 - (lo - nblk);
-                const int parts = cdiv(min(NB, n - b * NB), TR);
-                if (k < parts) q = k;
-                else t = ph == 0 ? (b + 1) * TPB + (k - parts) : b * TPB - 1 - (k - parts);
+                if (k == nbi) {                                // the chain item of block g (forward) / nblk-1-g
+                    b = ph == 0 ? g : nblk - 1 - g;
+                } else if (ph == 0) {                          // T(g-2, g + k)
+                    b = g - 2;
+                    t = g + k;
+                } else {                                       // T'(nblk+1-g, nblk-1-g-k)
+                    b = nblk + 1 - g;
+                    t = nblk - 1 - g - k;
+                }
             }
             s_item = item;
             s_ph = ph;
             s_b = b;
             s_t = t;
-            s_q = q;
         }
         __syncthreads();
         if (s_item >= total) break;
-        const int ph = s_ph, b = s_b, t = s_t, q = s_q;
-        const int r0 = b * NB, nb = min(NB, n - r0), parts = cdiv(nb, TR);
-        const bool part = t < 0;
-        // 1. the coefficient rows (independent of everything in flight)
-        const int ra = part ? r0 + q * TR : t * TR;      // first output row
-        const int nr = min(TR, (part ? r0 + nb : n) - ra);
-        if (part) {
-            const T* D = DT + (static_cast<size_t>(b) * 2 + ph) * NB * NB;   // D[p][i] = inv[i][p]
-            for (int p = warp; p < nb; p += nwarp)
-                if (lane < nr) Ls[lane * (NB + 1) + p] = D[static_cast<size_t>(p) * NB + q * TR + lane];
+        const int ph = s_ph, b = s_b, t = s_t;
+        const bool chain = t < 0;
+        const int r0 = (chain ? b : t) * NB, nr = min(NB, n - r0);          // rows this item writes
+        // coefficient columns: the neighbour block (chain) or block b (block item); -1: none
+        const int cb = chain ? (ph == 0 ? b - 1 : (b + 1 < nblk ? b + 1 : -1)) : b;
+        const int c0 = cb * NB, nc = cb >= 0 ? min(NB, n - c0) : 0;
+        // 1. coefficients (independent of everything in flight)
+        if (chain) {
+            solve_stage(Ds, CP, DM + (static_cast<size_t>(b) * 2 + ph) * NB * NB, NB, NB, NB, nr, nr, true);
+            if (cb >= 0) solve_stage(Cs, CP, MM + (static_cast<size_t>(b) * 2 + ph) * NB * NB, NB, NB, NB, nr, nc, true);
         } else if (chol && ph == 1) {
-            // U[ra + i][r0 + p] = L[r0 + p][ra + i]: lanes along the L row
-            for (int p = warp; p < nb; p += nwarp)
-                if (lane < nr) Ls[lane * (NB + 1) + p] = LU[idx(r0 + p, ra + lane, lda)];
+            solve_stage_t(Cs, CP, LU + idx(c0, r0, lda), lda, nr, nc);              // U[r0+i][c0+p] = L[c0+p][r0+i]
         } else {
-            for (int i = warp; i < nr; i += nwarp)
-                for (int p = lane; p < nb; p += 32) Ls[i * (NB + 1) + p] = LU[idx(ra + i, r0 + p, lda)];
+            solve_stage(Cs, CP, LU + idx(r0, c0, lda), lda, NB, NB, nr, nc, vec != 0);
         }
-        // 2. dependencies, all on earlier items
+        // 2. dependencies on earlier items: the rows' own earlier updates (and,
+        //    backward, their forward values) first
         if (tid == 0) {
             // test hook: the first item also waits on a counter nothing increments
             if (inject && s_item == 0) solve_wait(&sy->pad[0], 1, sy, wait_ns);
-            if (part) {
-                const int kb = ph == 0 ? b : nblk - 1 - b;
-                for (int u = b * TPB; u < min(ntile, (b + 1) * TPB); ++u)
-                    solve_wait(ph == 0 ? fdone + u : bdone + u, kb, sy, wait_ns);
-                if (ph == 1) solve_wait(xpf + b, parts, sy, wait_ns);
-            } else {
-                solve_wait(ph == 0 ? xpf + b : xpb + b, parts, sy, wait_ns);
-                if (ph == 1) {
-                    const int tb = t / TPB;
-                    solve_wait(xpf + tb, cdiv(min(NB, n - tb * NB), TR), sy, wait_ns);
+            if (chain) {
+                if (ph == 0) {
+                    solve_wait(fdone + b, b - 1, sy, wait_ns);
+                } else {
+                    solve_wait(xpf + b, 1, sy, wait_ns);                     // forward X_b
+                    solve_wait(bdone + b, nblk - b - 2, sy, wait_ns);
                 }
-                solve_wait(ph == 0 ? fdone + t : bdone + t, ph == 0 ? b : nblk - 1 - b, sy, wait_ns);
+            } else if (ph == 0) {
+                solve_wait(xpf + b, 1, sy, wait_ns);
+                solve_wait(fdone + t, b, sy, wait_ns);
+            } else {
+                solve_wait(xpb + b, 1, sy, wait_ns);
+                solve_wait(xpf + t, 1, sy, wait_ns);                         // forward X_t
+                solve_wait(bdone + t, nblk - 1 - b, sy, wait_ns);
             }
             __threadfence();
         }
         __syncthreads();
-        // 3. the right operand: the block's right-hand side (part) or its solution (tile);
-        //    written by other CTAs, so read past L1
-        const int key = (ph * 2 + (part ? 0 : 1)) * nblk + b;
-        if (bs_key != key) {
-            const T* src = part ? (ph == 0 ? Y : X) : (ph == 0 ? X : Y);
-            for (int e = tid; e < nb * NCW; e += kSolveThreads) Bs[e] = __ldcg(src + static_cast<size_t>(r0) * NCW + e);
-            bs_key = key;
-        }
+        // 3. operands written by other CTAs: 16-byte asynchronous copies, which
+        //    read through L2 only (the waits above ordered them after the writers)
+        solve_stage(Ws, NCW, (ph == 0 ? Y : X) + static_cast<size_t>(r0) * NCW, NCW, nr, NCW, nr, NCW, true);
+        if (!chain) solve_stage(Bs, NCW, (ph == 0 ? X : Y) + static_cast<size_t>(c0) * NCW, NCW, nc, NCW, nc, NCW, true);
+        cp_async_wait_all();
         __syncthreads();
-        // 4. 32 rows x NCW: out = Ls Bs
-        const int i = tid >> 3, cg = tid & 7;
-        T acc[MU];
-#pragma unroll
-        for (int k = 0; k < MU; ++k) acc[k] = T(0);
-        if (i < nr) {
-#pragma unroll 4
-            for (int p = 0; p < nb; ++p) {
-                const T l = Ls[i * (NB + 1) + p];
-#pragma unroll
-                for (int k = 0; k < MU; ++k) acc[k] = fma(l, Bs[p * NCW + cg + 8 * k], acc[k]);
+        // 4. products
+        T* dst = (ph == 0 ? (chain ? X : Y) : (chain ? Y : X)) + static_cast<size_t>(r0) * NCW;
+        if (chain) {
+            solve_rows<T, NCW>(Ds, CP, Ws, nr, nr, nullptr, 0, dst, NCW, false);   // inv(diag) times the rows
+            if (cb >= 0) {
+                // the neighbour's solution (the previous chain item), then the coupling
+                if (tid == 0) {
+                    solve_wait(ph == 0 ? xpf + cb : xpb + cb, 1, sy, wait_ns);
+                    __threadfence();
+                }
+                __syncthreads();
+                solve_stage(Bs, NCW, (ph == 0 ? X : Y) + static_cast<size_t>(c0) * NCW, NCW, nc, NCW, nc, NCW, true);
+                cp_async_wait_all();
+                __syncthreads();
+                // each thread reads back the entries it wrote above (same thread mapping)
+                solve_rows<T, NCW>(Cs, CP, Bs, nr, nc, dst, NCW, dst, NCW, true);
             }
-            if (part) {
-                T* row = (ph == 0 ? X : Y) + static_cast<size_t>(ra + i) * NCW;
-#pragma unroll
-                for (int k = 0; k < MU; ++k) row[cg + 8 * k] = acc[k];
-            } else {
-                T* row = (ph == 0 ? Y : X) + static_cast<size_t>(ra + i) * NCW;
-#pragma unroll
-                for (int k = 0; k < MU; ++k) row[cg + 8 * k] = __ldcg(row + cg + 8 * k) - acc[k];
-            }
+        } else {
+            solve_rows<T, NCW>(Cs, CP, Bs, nr, nc, Ws, NCW, dst, NCW, true);
         }
         __threadfence();
         __syncthreads();
         if (tid == 0) {
-            if (part) atomicAdd(ph == 0 ? xpf + b : xpb + b, 1);
+            if (chain) atomicAdd(ph == 0 ? xpf + b : xpb + b, 1);
             else atomicAdd(ph == 0 ? fdone + t : bdone + t, 1);
         }
     }
@@ -317,10 +479,10 @@ __global__ void __launch_bounds__(kSolveThreads) solve_items_kernel(int n, const
 template <typename T, int NCW>
 static size_t solve_smem() {
     constexpr int NB = SolveNB<T>::value;
-    return (static_cast<size_t>(kSolveTile) * (NB + 1) + static_cast<size_t>(NB) * NCW) * sizeof(T);
+    return (2 * static_cast<size_t>(NB) * solve_cp<T>() + 2 * static_cast<size_t>(NB) * NCW) * sizeof(T);
 }
 
-// CTAs of the item kernel: as many as fit on the device, up to 4 per SM
+// CTAs of the item kernel: as many as fit on the device, up to 2 per SM
 // (none need to be resident together).
 template <typename T, int NCW>
 static int solve_grid() {
@@ -334,7 +496,7 @@ static int solve_grid() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_items_kernel<T, NCW>, kSolveThreads, smem);
     cudaGetLastError();
     if (per < 1 || sms < 1) return -1;
-    return sms * (per < 4 ? per : 4);
+    return sms * (per < 2 ? per : 2);
 }
 
 template <typename T, int NCW>
@@ -343,8 +505,10 @@ static int solve_launch(int n, const SolvePlan<T>& p, T* Y, T* X, int* fdone, in
     const int G = solve_grid<T, NCW>();
     if (G <= 0) return LU_EUNSUPPORTED;
     const WaitCfg wc = wait_cfg(LU_WAIT_SITE_SOLVE);
+    constexpr int V = 16 / static_cast<int>(sizeof(T));
+    const int vec = (reinterpret_cast<uintptr_t>(p.LU) & 15) == 0 && (p.lda % V) == 0 ? 1 : 0;
     solve_items_kernel<T, NCW><<<G, kSolveThreads, solve_smem<T, NCW>(), s>>>(
-        n, p.LU, p.lda, p.DT, p.off, Y, X, fdone, bdone, xpf, xpb, sy, p.chol, wc.wait_ns, wc.inject);
+        n, p.LU, p.lda, p.DT, p.M, p.off, Y, X, fdone, bdone, xpf, xpb, sy, p.chol, vec, wc.wait_ns, wc.inject);
     count_launches(1);
     return 0;
 }
@@ -390,6 +554,8 @@ int solve_plan_make(int n, const T* LU, int lda, const int* piv, SolvePlan<T>* p
     if (cudaMallocAsync(reinterpret_cast<void**>(&p->perm), sizeof(int) * static_cast<size_t>(n), s) != cudaSuccess ||
         cudaMallocAsync(reinterpret_cast<void**>(&p->DT), sizeof(T) * static_cast<size_t>(nblk) * 2 * NB * NB, s) !=
             cudaSuccess ||
+        cudaMallocAsync(reinterpret_cast<void**>(&p->M), sizeof(T) * static_cast<size_t>(nblk) * 2 * NB * NB, s) !=
+            cudaSuccess ||
         cudaMallocAsync(reinterpret_cast<void**>(&p->off), sizeof(int) * (2 * static_cast<size_t>(nblk) + 1), s) !=
             cudaSuccess) {
         cudaGetLastError();
@@ -421,6 +587,14 @@ int solve_plan_make(int n, const T* LU, int lda, const int* piv, SolvePlan<T>* p
     }
     LU_LAUNCHED();
     {
+        const size_t csmem = 2 * static_cast<size_t>(NB) * (NB + 1) * sizeof(T);
+        if (int rc_ = smem_attr(couple_kernel<T>, csmem)) return rc_;
+        ProfScope ps(LU_PROF_SOLVE, s);
+        couple_kernel<T><<<dim3(nblk, 2), 256, csmem, s>>>(n, LU, lda, p->DT, p->M, p->chol);
+        count_launches(1);
+    }
+    LU_LAUNCHED();
+    {
         const int nbv = NB;
         LU_TRY(cudaMemcpyAsync(p->off, &nbv, sizeof(int), cudaMemcpyHostToDevice, s));
         ProfScope ps(LU_PROF_SOLVE, s);
@@ -435,9 +609,11 @@ template <typename T>
 void solve_plan_free(SolvePlan<T>* p, cudaStream_t s) {
     if (p->perm) cudaFreeAsync(p->perm, s);
     if (p->DT) cudaFreeAsync(p->DT, s);
+    if (p->M) cudaFreeAsync(p->M, s);
     if (p->off) cudaFreeAsync(p->off, s);
     p->perm = nullptr;
     p->DT = nullptr;
+    p->M = nullptr;
     p->off = nullptr;
 }
 
@@ -446,9 +622,9 @@ int solve_plan_apply(const SolvePlan<T>& p, int nrhs, T* B, int ldb, cudaStream_
     constexpr int NB = SolveNB<T>::value;
     const int n = p.n;
     if (n == 0 || nrhs == 0) return 0;
-    const int nblk = cdiv(n, NB), ntile = cdiv(n, kSolveTile);
+    const int nblk = cdiv(n, NB);
     const size_t vs = static_cast<size_t>(n) * kSolveRhs;
-    const size_t flags = sizeof(SolveSync) + sizeof(int) * (2 * static_cast<size_t>(ntile) + 2 * nblk);
+    const size_t flags = sizeof(SolveSync) + sizeof(int) * (4 * static_cast<size_t>(nblk));
     const size_t fbytes = (flags + 255) / 256 * 256;
     void* ws = nullptr;
     if (cudaMallocAsync(&ws, fbytes + sizeof(T) * 2 * vs, s) != cudaSuccess) {
@@ -457,8 +633,8 @@ int solve_plan_apply(const SolvePlan<T>& p, int nrhs, T* B, int ldb, cudaStream_
     }
     SolveSync* sy = static_cast<SolveSync*>(ws);
     int* fdone = reinterpret_cast<int*>(sy + 1);
-    int* bdone = fdone + ntile;
-    int* xpf = bdone + ntile;
+    int* bdone = fdone + nblk;
+    int* xpf = bdone + nblk;
     int* xpb = xpf + nblk;
     T* Y = reinterpret_cast<T*>(static_cast<unsigned char*>(ws) + fbytes);
     T* X = Y + vs;

@@ -86,12 +86,12 @@ class Server {
 
     // what a request keeps on the device when its factors are cached: A,
     // the binary32 factors and pivots, and (slot path) the solve plan's
-    // diagonal-block inverses (2 x 128 x 128 floats per 128 rows) and
-    // permutation
+    // diagonal-block inverses and coupling blocks (2 + 2 blocks of 128 x 128
+    // floats per 128 rows, the last block padded) and permutation
     static size_t persistent_bytes(int n, bool batched) {
         const size_t nn = static_cast<size_t>(n) * n;
         size_t b = nn * (8 + 4) + static_cast<size_t>(n) * 4 + 4096;
-        if (!batched) b += static_cast<size_t>(n) * (1024 + 4) + 4096;
+        if (!batched) b += static_cast<size_t>((n + 127) / 128) * 128 * 2048 + static_cast<size_t>(n) * 4 + 4096;
         return b;
     }
     // what it needs only while it runs

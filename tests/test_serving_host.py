@@ -24,7 +24,7 @@ def req_bytes(n, nrhs, batched=None):
     per = n * n * 12 + n * 4 + 4096
     if batched:
         return per + vs * (3 * 8 + 4) + 16 * nrhs + 4096
-    per += n * (1024 + 4) + 4096
+    per += -(-n // 128) * 128 * 2048 + n * 4 + 4096
     trans = 2 * vs * 8 + vs * (8 + 4 + 8 * (2 * 30 + 2)) + n * 16 * 4 + (304 * nrhs * 4 + 32 * 16 * nrhs + 16 * nrhs) * 8 \
         + 4096 + n * (4 * 1040 + 2048)
     return per + trans
@@ -180,4 +180,4 @@ def test_budget_accounting_matches_cache_entries():
         st = srv.stats()
     assert st["cache_entries"] == 5
     assert st["used_bytes"] == 3 * (300 * 300 * 12 + 300 * 4 + 4096) + \
-        2 * (1100 * 1100 * 12 + 1100 * 4 + 4096 + 1100 * (1024 + 4) + 4096)
+        2 * (1100 * 1100 * 12 + 1100 * 4 + 4096 + 9 * 128 * 2048 + 1100 * 4 + 4096)
