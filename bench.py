@@ -273,6 +273,7 @@ def run_mixed(a, dev, t_fp64_factor=None, warmup=1, steps=2, kappas=(1e2, 1e4, 1
             case = {"kappa": kappa, "precision": pname, "ms": 1e3 * t, "solves_per_s": 1.0 / t,
                     "iters": res["iters"], "gmres_iters": res["gmres_iters"], "path": res["path"],
                     "krylov_cycles": {"binary32_products": res["cycles32"], "binary64_products": res["cycles64"]},
+                    "inner_steps": res["inner_steps"],
                     "final_precision": ["f64", "f32", "bf16", "fp8"][res["precision"]],
                     "eta": res["eta"], "fwd_err": fwd,
                     "kernel_ms": {k: round(v["ms"], 2) for k, v in prof.items()},

@@ -309,7 +309,9 @@ typedef struct {
                                multiplies first, binary64 from the first cycle
                                that cuts eta by less than 10x; 1 binary64
                                only; 2 binary32 multiplies only               */
-    int reserved[3];        /* must be zero                                     */
+    int inner_steps;        /* binary32-product inner steps per classical step
+                               (0: default 3; negative: none)                  */
+    int reserved[2];        /* must be zero                                     */
 } ir_opts;
 
 typedef struct {
@@ -324,6 +326,7 @@ typedef struct {
     int refactors;          /* times the ladder moved up a precision            */
     int cycles32;           /* FGMRES cycles run with binary32-multiply products */
     int cycles64;           /* FGMRES cycles run with binary64 products          */
+    int inner_steps;        /* binary32-product inner steps of classical steps   */
 } ir_result;
 
 /*
@@ -332,8 +335,11 @@ typedef struct {
  * B (n x nrhs, ldb) are read only; X (n x nrhs, ldx) receives the solution;
  * all three are device arrays.  res is a HOST pointer.  The refinement
  * decides on the host when to stop, so this call synchronizes `stream` and
- * returns when X is final.  Classical refinement (x += LU^{-1} r) runs while
- * each step cuts eta by 4x or more; after that the correction equation is
+ * returns when X is final.  Classical refinement runs while each step cuts
+ * eta by 4x or more: from the binary64 residual r it solves A d = r with up
+ * to inner_steps binary32-product steps (d += LU^{-1} (r - A d), A d with
+ * binary32 multiplies, stopping once the inner residual stops shrinking by
+ * 2x or falls below 1e-6 |r|), then x += d.  After that the correction equation is
  * solved by right-preconditioned flexible GMRES (binary64 Arnoldi and
  * Gram-Schmidt, the fp32 LU solve as preconditioner).  Its products A z
  * first use binary32 multiplies (A and z rounded to binary32, 32-term

@@ -41,14 +41,14 @@ class lu_opts(ctypes.Structure):
 class ir_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("b", ctypes.c_int), ("h", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("krylov_products", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("inner_steps", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class ir_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("gmres_iters", ctypes.c_int), ("path", ctypes.c_int),
                 ("info", ctypes.c_int), ("eta", ctypes.c_double), ("eta0", ctypes.c_double),
                 ("precision", ctypes.c_int), ("refactors", ctypes.c_int), ("cycles32", ctypes.c_int),
-                ("cycles64", ctypes.c_int)]
+                ("cycles64", ctypes.c_int), ("inner_steps", ctypes.c_int)]
 
 
 class serve_cfg(ctypes.Structure):

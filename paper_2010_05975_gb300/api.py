@@ -232,11 +232,12 @@ def lu_residual(A: torch.Tensor, X: torch.Tensor, B: torch.Tensor, R: torch.Tens
 
 def ir_solve(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor | None = None, precision: int = nat.LU_PREC_BF16,
              tol: float = 1e-12, b: int = 0, h: int = 0, max_iter: int = 0, gmres_restart: int = 0,
-             krylov_products: int = 0, stream=None):
+             krylov_products: int = 0, inner_steps: int = 0, stream=None):
     """Solve A X = B (float64 CUDA tensors) with a low-precision factorization
     and float64 refinement.  krylov_products: 0 adaptive (binary32 multiplies
-    first), 1 binary64 only, 2 binary32 multiplies only.  Synchronizes the
-    stream; returns (X, result)."""
+    first), 1 binary64 only, 2 binary32 multiplies only.  inner_steps:
+    binary32-product inner steps per classical step (0 default, < 0 none).
+    Synchronizes the stream; returns (X, result)."""
     _require(A, "A", torch.float64, 2)
     n = A.shape[0]
     B2 = B if B.dim() == 2 else B.view(n, 1)
@@ -244,7 +245,7 @@ def ir_solve(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor | None = None, pr
     if X is None:
         X = torch.empty_like(B2)
     X2 = X if X.dim() == 2 else X.view(n, 1)
-    opts = nat.ir_opts(precision, b, h, tol, max_iter, gmres_restart, krylov_products)
+    opts = nat.ir_opts(precision, b, h, tol, max_iter, gmres_restart, krylov_products, inner_steps)
     res = nat.ir_result()
     rc = nat.library().ir_solve(n, B2.shape[1], A.data_ptr(), max(A.stride(0), 1), B2.data_ptr(),
                                 max(B2.stride(0), 1), X2.data_ptr(), max(X2.stride(0), 1), ctypes.byref(opts),
@@ -252,7 +253,7 @@ def ir_solve(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor | None = None, pr
     nat.check("ir_solve", rc)
     out = {"iters": res.iters, "gmres_iters": res.gmres_iters, "path": res.path, "info": res.info,
            "eta": res.eta, "eta0": res.eta0, "precision": res.precision, "refactors": res.refactors,
-           "cycles32": res.cycles32, "cycles64": res.cycles64}
+           "cycles32": res.cycles32, "cycles64": res.cycles64, "inner_steps": res.inner_steps}
     return X, out
 
 

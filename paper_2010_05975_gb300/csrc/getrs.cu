@@ -476,9 +476,168 @@ __global__ void __launch_bounds__(kSolveThreads) solve_items_kernel(int n, const
     }
 }
 
+constexpr int kPartsTile = 32;           // rows per part / tile of the binary64 list
+constexpr int kPartsThreads = 256;
+
+// The binary64 list: items before forward step b / backward step b,
+// off[0..2*nblk], built once per plan (the block size arrives in off[0]).
+// Step b: the 32-row parts of the diagonal solve, then every tile below
+// (forward) or above (backward).
+__global__ void solve_parts_offsets_kernel(int n, int* __restrict__ off) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    constexpr int TR = kPartsTile;
+    const int ntile = cdiv(n, TR);
+    const int NB = off[0];
+    const int nblk = cdiv(n, NB);
+    const int tpb = NB / TR;
+    int acc = 0;
+    for (int b = 0; b < nblk; ++b) {                    // forward
+        off[b] = acc;
+        const int parts = cdiv(min(NB, n - b * NB), TR);
+        acc += parts + ntile - min(ntile, (b + 1) * tpb);
+    }
+    for (int st = 0; st < nblk; ++st) {                 // backward, last block first
+        const int b = nblk - 1 - st;
+        off[nblk + st] = acc;
+        const int parts = cdiv(min(NB, n - b * NB), TR);
+        acc += parts + b * tpb;
+    }
+    off[2 * nblk] = acc;
+}
+
+// The binary64 substitution (the DFMA pipe, about 2 per clock per SM, makes a
+// one-CTA chain step slow, so a step's diagonal solve is split into 32-row
+// parts on several CTAs): forward (L: Y -> X) then backward (U: X -> Y);
+// right-hand sides row-major with stride NCW (columns >= nc are zero and
+// stay zero).  With chol set, U is L^T: the backward tiles read L
+// transposed.
+template <typename T, int NCW>
+__global__ void __launch_bounds__(kPartsThreads) solve_parts_kernel(int n, const T* __restrict__ LU, int lda,
+                                                                    const T* __restrict__ DT,
+                                                                    const int* __restrict__ off, T* Y, T* X,
+                                                                    int* fdone, int* bdone, int* xpf, int* xpb,
+                                                                    SolveSync* sy, int chol,
+                                                                    unsigned long long wait_ns, int inject) {
+    constexpr int NB = SolveNB<T>::value;
+    constexpr int TR = kPartsTile;
+    constexpr int TPB = NB / TR;                     // tiles (and solve parts) per block
+    constexpr int MU = NCW / 8;                      // columns per thread
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Ls = reinterpret_cast<T*>(smem_raw);          // TR x (NB+1): the item's coefficient rows
+    T* Bs = Ls + TR * (NB + 1);                      // NB x NCW: the right operand
+    __shared__ int s_item, s_ph, s_b, s_t, s_q;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = kPartsThreads / 32;
+    const int nblk = cdiv(n, NB), ntile = cdiv(n, TR);
+    const int total = off[2 * nblk];
+    int bs_key = -1;                                 // which block Bs holds: (ph * 2 + kind) * nblk + b
+    for (;;) {
+        if (tid == 0) {
+            const int item = atomicAdd(&sy->next, 1);
+            int ph = 0, b = 0, t = -1, q = 0;
+            if (item < total) {
+                int lo = 0, hi = 2 * nblk - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (off[mid] <= item) lo = mid; else hi = mid - 1;
+                }
+                const int k = item - off[lo];
+                ph = lo < nblk ? 0 : 1;
+                b = ph == 0 ? lo : nblk - 1 - (lo - nblk);
+                const int parts = cdiv(min(NB, n - b * NB), TR);
+                if (k < parts) q = k;
+                else t = ph == 0 ? (b + 1) * TPB + (k - parts) : b * TPB - 1 - (k - parts);
+            }
+            s_item = item;
+            s_ph = ph;
+            s_b = b;
+            s_t = t;
+            s_q = q;
+        }
+        __syncthreads();
+        if (s_item >= total) break;
+        const int ph = s_ph, b = s_b, t = s_t, q = s_q;
+        const int r0 = b * NB, nb = min(NB, n - r0), parts = cdiv(nb, TR);
+        const bool part = t < 0;
+        // 1. the coefficient rows (independent of everything in flight)
+        const int ra = part ? r0 + q * TR : t * TR;      // first output row
+        const int nr = min(TR, (part ? r0 + nb : n) - ra);
+        if (part) {
+            const T* D = DT + (static_cast<size_t>(b) * 2 + ph) * NB * NB;   // D[i][p] = inv[i][p]
+            for (int i = warp; i < nr; i += nwarp)
+                for (int p = lane; p < nb; p += 32) Ls[i * (NB + 1) + p] = D[static_cast<size_t>(q * TR + i) * NB + p];
+        } else if (chol && ph == 1) {
+            // U[ra + i][r0 + p] = L[r0 + p][ra + i]: lanes along the L row
+            for (int p = warp; p < nb; p += nwarp)
+                if (lane < nr) Ls[lane * (NB + 1) + p] = LU[idx(r0 + p, ra + lane, lda)];
+        } else {
+            for (int i = warp; i < nr; i += nwarp)
+                for (int p = lane; p < nb; p += 32) Ls[i * (NB + 1) + p] = LU[idx(ra + i, r0 + p, lda)];
+        }
+        // 2. dependencies, all on earlier items
+        if (tid == 0) {
+            // test hook: the first item also waits on a counter nothing increments
+            if (inject && s_item == 0) solve_wait(&sy->pad[0], 1, sy, wait_ns);
+            if (part) {
+                const int kb = ph == 0 ? b : nblk - 1 - b;
+                for (int u = b * TPB; u < min(ntile, (b + 1) * TPB); ++u)
+                    solve_wait(ph == 0 ? fdone + u : bdone + u, kb, sy, wait_ns);
+                if (ph == 1) solve_wait(xpf + b, parts, sy, wait_ns);
+            } else {
+                solve_wait(ph == 0 ? xpf + b : xpb + b, parts, sy, wait_ns);
+                if (ph == 1) {
+                    const int tb = t / TPB;
+                    solve_wait(xpf + tb, cdiv(min(NB, n - tb * NB), TR), sy, wait_ns);
+                }
+                solve_wait(ph == 0 ? fdone + t : bdone + t, ph == 0 ? b : nblk - 1 - b, sy, wait_ns);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        // 3. the right operand: the block's right-hand side (part) or its solution (tile);
+        //    written by other CTAs, so read past L1
+        const int key = (ph * 2 + (part ? 0 : 1)) * nblk + b;
+        if (bs_key != key) {
+            const T* src = part ? (ph == 0 ? Y : X) : (ph == 0 ? X : Y);
+            for (int e = tid; e < nb * NCW; e += kPartsThreads) Bs[e] = __ldcg(src + static_cast<size_t>(r0) * NCW + e);
+            bs_key = key;
+        }
+        __syncthreads();
+        // 4. 32 rows x NCW: out = Ls Bs
+        const int i = tid >> 3, cg = tid & 7;
+        T acc[MU];
+#pragma unroll
+        for (int k = 0; k < MU; ++k) acc[k] = T(0);
+        if (i < nr) {
+#pragma unroll 4
+            for (int p = 0; p < nb; ++p) {
+                const T l = Ls[i * (NB + 1) + p];
+#pragma unroll
+                for (int k = 0; k < MU; ++k) acc[k] = fma(l, Bs[p * NCW + cg + 8 * k], acc[k]);
+            }
+            if (part) {
+                T* row = (ph == 0 ? X : Y) + static_cast<size_t>(ra + i) * NCW;
+#pragma unroll
+                for (int k = 0; k < MU; ++k) row[cg + 8 * k] = acc[k];
+            } else {
+                T* row = (ph == 0 ? Y : X) + static_cast<size_t>(ra + i) * NCW;
+#pragma unroll
+                for (int k = 0; k < MU; ++k) row[cg + 8 * k] = __ldcg(row + cg + 8 * k) - acc[k];
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            if (part) atomicAdd(ph == 0 ? xpf + b : xpb + b, 1);
+            else atomicAdd(ph == 0 ? fdone + t : bdone + t, 1);
+        }
+    }
+}
+
 template <typename T, int NCW>
 static size_t solve_smem() {
     constexpr int NB = SolveNB<T>::value;
+    if constexpr (sizeof(T) == 8)
+        return (static_cast<size_t>(kPartsTile) * (NB + 1) + static_cast<size_t>(NB) * NCW) * sizeof(T);
     return (2 * static_cast<size_t>(NB) * solve_cp<T>() + 2 * static_cast<size_t>(NB) * NCW) * sizeof(T);
 }
 
@@ -492,6 +651,13 @@ static int solve_grid() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = solve_smem<T, NCW>();
+    if constexpr (sizeof(T) == 8) {
+        if (smem_attr(solve_parts_kernel<T, NCW>, smem) != 0) return -1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_parts_kernel<T, NCW>, kPartsThreads, smem);
+        cudaGetLastError();
+        if (per < 1 || sms < 1) return -1;
+        return sms * (per < 4 ? per : 4);
+    }
     if (smem_attr(solve_items_kernel<T, NCW>, smem) != 0) return -1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solve_items_kernel<T, NCW>, kSolveThreads, smem);
     cudaGetLastError();
@@ -505,10 +671,15 @@ static int solve_launch(int n, const SolvePlan<T>& p, T* Y, T* X, int* fdone, in
     const int G = solve_grid<T, NCW>();
     if (G <= 0) return LU_EUNSUPPORTED;
     const WaitCfg wc = wait_cfg(LU_WAIT_SITE_SOLVE);
-    constexpr int V = 16 / static_cast<int>(sizeof(T));
-    const int vec = (reinterpret_cast<uintptr_t>(p.LU) & 15) == 0 && (p.lda % V) == 0 ? 1 : 0;
-    solve_items_kernel<T, NCW><<<G, kSolveThreads, solve_smem<T, NCW>(), s>>>(
-        n, p.LU, p.lda, p.DT, p.M, p.off, Y, X, fdone, bdone, xpf, xpb, sy, p.chol, vec, wc.wait_ns, wc.inject);
+    if constexpr (sizeof(T) == 8) {
+        solve_parts_kernel<T, NCW><<<G, kPartsThreads, solve_smem<T, NCW>(), s>>>(
+            n, p.LU, p.lda, p.DT, p.off, Y, X, fdone, bdone, xpf, xpb, sy, p.chol, wc.wait_ns, wc.inject);
+    } else {
+        constexpr int V = 16 / static_cast<int>(sizeof(T));
+        const int vec = (reinterpret_cast<uintptr_t>(p.LU) & 15) == 0 && (p.lda % V) == 0 ? 1 : 0;
+        solve_items_kernel<T, NCW><<<G, kSolveThreads, solve_smem<T, NCW>(), s>>>(
+            n, p.LU, p.lda, p.DT, p.M, p.off, Y, X, fdone, bdone, xpf, xpb, sy, p.chol, vec, wc.wait_ns, wc.inject);
+    }
     count_launches(1);
     return 0;
 }
@@ -554,8 +725,9 @@ int solve_plan_make(int n, const T* LU, int lda, const int* piv, SolvePlan<T>* p
     if (cudaMallocAsync(reinterpret_cast<void**>(&p->perm), sizeof(int) * static_cast<size_t>(n), s) != cudaSuccess ||
         cudaMallocAsync(reinterpret_cast<void**>(&p->DT), sizeof(T) * static_cast<size_t>(nblk) * 2 * NB * NB, s) !=
             cudaSuccess ||
-        cudaMallocAsync(reinterpret_cast<void**>(&p->M), sizeof(T) * static_cast<size_t>(nblk) * 2 * NB * NB, s) !=
-            cudaSuccess ||
+        (sizeof(T) == 4 &&
+         cudaMallocAsync(reinterpret_cast<void**>(&p->M), sizeof(T) * static_cast<size_t>(nblk) * 2 * NB * NB, s) !=
+             cudaSuccess) ||
         cudaMallocAsync(reinterpret_cast<void**>(&p->off), sizeof(int) * (2 * static_cast<size_t>(nblk) + 1), s) !=
             cudaSuccess) {
         cudaGetLastError();
@@ -586,7 +758,7 @@ int solve_plan_make(int n, const T* LU, int lda, const int* piv, SolvePlan<T>* p
         count_launches(1);
     }
     LU_LAUNCHED();
-    {
+    if (sizeof(T) == 4) {
         const size_t csmem = 2 * static_cast<size_t>(NB) * (NB + 1) * sizeof(T);
         if (int rc_ = smem_attr(couple_kernel<T>, csmem)) return rc_;
         ProfScope ps(LU_PROF_SOLVE, s);
@@ -598,7 +770,10 @@ int solve_plan_make(int n, const T* LU, int lda, const int* piv, SolvePlan<T>* p
         const int nbv = NB;
         LU_TRY(cudaMemcpyAsync(p->off, &nbv, sizeof(int), cudaMemcpyHostToDevice, s));
         ProfScope ps(LU_PROF_SOLVE, s);
-        solve_offsets_kernel<<<1, 32, 0, s>>>(n, p->off);
+        if (sizeof(T) == 8)
+            solve_parts_offsets_kernel<<<1, 32, 0, s>>>(n, p->off);
+        else
+            solve_offsets_kernel<<<1, 32, 0, s>>>(n, p->off);
         count_launches(1);
     }
     LU_LAUNCHED();
@@ -622,9 +797,10 @@ int solve_plan_apply(const SolvePlan<T>& p, int nrhs, T* B, int ldb, cudaStream_
     constexpr int NB = SolveNB<T>::value;
     const int n = p.n;
     if (n == 0 || nrhs == 0) return 0;
-    const int nblk = cdiv(n, NB);
+    const int nblk = cdiv(n, NB), ntile = cdiv(n, kPartsTile);
+    const int nflag = sizeof(T) == 8 ? ntile : nblk;           // per-tile (binary64) or per-block counters
     const size_t vs = static_cast<size_t>(n) * kSolveRhs;
-    const size_t flags = sizeof(SolveSync) + sizeof(int) * (4 * static_cast<size_t>(nblk));
+    const size_t flags = sizeof(SolveSync) + sizeof(int) * (2 * static_cast<size_t>(nflag) + 2 * nblk);
     const size_t fbytes = (flags + 255) / 256 * 256;
     void* ws = nullptr;
     if (cudaMallocAsync(&ws, fbytes + sizeof(T) * 2 * vs, s) != cudaSuccess) {
@@ -633,8 +809,8 @@ int solve_plan_apply(const SolvePlan<T>& p, int nrhs, T* B, int ldb, cudaStream_
     }
     SolveSync* sy = static_cast<SolveSync*>(ws);
     int* fdone = reinterpret_cast<int*>(sy + 1);
-    int* bdone = fdone + nblk;
-    int* xpf = bdone + nblk;
+    int* bdone = fdone + nflag;
+    int* xpf = bdone + nflag;
     int* xpb = xpf + nblk;
     T* Y = reinterpret_cast<T*>(static_cast<unsigned char*>(ws) + fbytes);
     T* X = Y + vs;

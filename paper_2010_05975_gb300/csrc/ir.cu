@@ -6,7 +6,10 @@
 //
 //   x0 = (float solve with the low-precision factors)
 //   repeat: r = b - A x (fp64); eta = ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf)
-//           stop at eta <= tol;  d = LU^{-1} (r / ||r||) * ||r|| (fp32 solve); x += d
+//           stop at eta <= tol;  d = LU^{-1} (r / ||r||) * ||r|| (fp32 solve);
+//           up to J inner steps d += LU^{-1} (r - A d) with the products A d
+//           in binary32 multiplies (matvec32_kernel), while the inner
+//           residual keeps shrinking by 2x and stays above 1e-6 ||r||; x += d
 // Once a classical step cuts eta by less than 4x, the correction equation
 // A d = r is solved instead (for the rest of the solve) by
 // right-preconditioned flexible GMRES (binary64 Arnoldi, preconditioner =
@@ -363,6 +366,18 @@ __global__ void eta_kernel(int nr, const double* __restrict__ r, const double* _
     }
 }
 
+// W = R - W and D += W, elementwise over n x nrhs (row-major, stride nrhs).
+__global__ void sub_from_kernel(long long tot, const double* __restrict__ R, double* __restrict__ W) {
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < tot;
+         e += static_cast<long long>(gridDim.x) * blockDim.x)
+        W[e] = R[e] - W[e];
+}
+__global__ void add_to_kernel(long long tot, const double* __restrict__ W, double* __restrict__ D) {
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < tot;
+         e += static_cast<long long>(gridDim.x) * blockDim.x)
+        D[e] += W[e];
+}
+
 static int grid_for(long long tot) {
     long long g = (tot + 255) / 256;
     return static_cast<int>(g < 4096 ? (g > 0 ? g : 1) : 4096);
@@ -547,6 +562,49 @@ int precond_apply(IrCtx& c, const double* V, double* Z, double* scale) {
 int to_host(cudaStream_t s, const double* d, double* h, int count) {
     LU_TRY(cudaMemcpyAsync(h, d, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
     LU_TRY(cudaStreamSynchronize(s));
+    return 0;
+}
+
+// The correction of one classical step: D = M^{-1} R, then up to J inner
+// steps D += M^{-1} (R - A D) with A D in binary32 multiplies, stopping
+// before a step whose residual E = R - A D is already within 1e-6 of R
+// (the products' accuracy) or did not shrink by 2x in some column.  W is
+// scratch (n x nrhs); *steps counts the inner steps applied.
+int inner_refine(IrCtx& c, int J, double* D, double* W, int* steps) {
+    const int n = c.n, nr = c.nrhs;
+    const long long tot = static_cast<long long>(n) * nr;
+    double* nrm = c.vec + 6 * nr;
+    std::vector<double> rn(nr), prev(nr), en(nr);
+    if (int rc = col_reduce(n, nr, c.R, nr, nullptr, 0, 0, c.part, nrm, c.s)) return rc;
+    if (int rc = to_host(c.s, nrm, rn.data(), nr)) return rc;
+    prev = rn;
+    if (int rc = precond_apply(c, c.R, D, c.vec)) return rc;
+    for (int j = 0; j < J; ++j) {
+        if (int rc = matvec32(n, nr, c.A, c.lda, D, nr, W, nr, c.zf, c.s)) return rc;     // W = A D
+        {
+            ProfScope ps(LU_PROF_OTHER, c.s);
+            sub_from_kernel<<<grid_for(tot), 256, 0, c.s>>>(tot, c.R, W);                  // W = R - A D
+            count_launches(1);
+        }
+        LU_LAUNCHED();
+        if (int rc = col_reduce(n, nr, W, nr, nullptr, 0, 0, c.part, nrm, c.s)) return rc;
+        if (int rc = to_host(c.s, nrm, en.data(), nr)) return rc;
+        bool small = true, shrinks = true;
+        for (int k = 0; k < nr; ++k) {
+            if (en[k] > 1e-6 * rn[k]) small = false;
+            if (en[k] > 0.5 * prev[k]) shrinks = false;
+        }
+        if (small || !shrinks) break;
+        if (int rc = precond_apply(c, W, W, c.vec)) return rc;
+        {
+            ProfScope ps(LU_PROF_OTHER, c.s);
+            add_to_kernel<<<grid_for(tot), 256, 0, c.s>>>(tot, W, D);
+            count_launches(1);
+        }
+        LU_LAUNCHED();
+        *steps += 1;
+        prev = en;
+    }
     return 0;
 }
 
@@ -767,6 +825,9 @@ int ir_refine(IrFactors* fac, const double* A, int lda, int nrhs, const double* 
     c.vec = dev.alloc<double>(8 * static_cast<size_t>(nrhs) + 8);
     c.an = dev.alloc<double>(1);
     double* bmax = dev.alloc<double>(nrhs);
+    const int inner = opt.inner_steps < 0 ? 0 : (opt.inner_steps == 0 ? 3 : opt.inner_steps);
+    double* Dd = inner > 0 ? dev.alloc<double>(vs) : nullptr;
+    double* Wd = inner > 0 ? dev.alloc<double>(vs) : nullptr;
     if (!dev.ok) return LU_ENOMEM;
     double* V = nullptr;
     double* Z = nullptr;
@@ -838,7 +899,12 @@ int ir_refine(IrFactors* fac, const double* A, int lda, int nrhs, const double* 
             prev = em;
             ++total_it;
             if (!krylov) {
-                if (int rc = precond_apply(c, c.R, c.R, c.vec)) return rc;
+                if (inner > 0) {
+                    if (int rc = inner_refine(c, inner, Dd, Wd, &res->inner_steps)) return rc;
+                    std::swap(c.R, Dd);             // X += D below
+                } else if (int rc = precond_apply(c, c.R, c.R, c.vec)) {
+                    return rc;
+                }
                 double* one = c.vec + 5 * nrhs;
                 std::vector<double> ones(nrhs, 1.0);
                 LU_TRY(cudaMemcpyAsync(one, ones.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, stream));
@@ -884,7 +950,7 @@ int ir_refine(IrFactors* fac, const double* A, int lda, int nrhs, const double* 
 size_t ir_workspace_bytes(int n, int nrhs, int restart) {
     const size_t vs = static_cast<size_t>(n) * nrhs;
     if (restart <= 0) restart = 30;
-    return vs * (8 + 4 + 8 * (2 * static_cast<size_t>(restart) + 2)) + static_cast<size_t>(n) * kMv32RG * 4 +
+    return vs * (8 + 4 + 8 * (2 * static_cast<size_t>(restart) + 2) + 16) + static_cast<size_t>(n) * kMv32RG * 4 +
            (static_cast<size_t>(kRedBlocks) * nrhs * 4 + static_cast<size_t>(restart + 2) * 16 * nrhs + 16 * nrhs) * 8 +
            4096;
 }

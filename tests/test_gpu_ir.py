@@ -101,3 +101,24 @@ def test_ir_rejects_bad_krylov_option():
     A = torch.eye(8, dtype=torch.float64, device="cuda")
     with pytest.raises(nat.LuError):
         g.ir_solve(A, torch.ones(8, 1, dtype=torch.float64, device="cuda"), krylov_products=3)
+
+
+@pytest.mark.parametrize("inner", [-1, 0, 5])
+def test_ir_inner_steps(oracle_mod, inner):
+    """Classical steps with and without the binary32-product inner steps all
+    reach 1e-12; with them (bf16, kappa = 1e2) fewer binary64 residuals are
+    needed than without."""
+    torch = cuda_or_fail()
+    g = lib()
+    n, nrhs = 1024, 8
+    A, B, Xt = make_problem(n, 1e2, nrhs, seed=61)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    X, res = g.ir_solve(dA, dB, precision=BF16, inner_steps=inner)
+    eta = oracle_mod.backward_error(A, B, X.cpu().numpy())
+    assert res["eta"] <= 1e-12 and eta.max() <= 1e-12, (res, eta.max())
+    if inner < 0:
+        assert res["inner_steps"] == 0
+    else:
+        _, plain = g.ir_solve(dA, dB, precision=BF16, inner_steps=-1)
+        if res["path"] == 0 and plain["path"] == 0:
+            assert res["inner_steps"] >= 1 and res["iters"] < plain["iters"], (res, plain)

@@ -25,7 +25,7 @@ def req_bytes(n, nrhs, batched=None):
     if batched:
         return per + vs * (3 * 8 + 4) + 16 * nrhs + 4096
     per += -(-n // 128) * 128 * 2048 + n * 4 + 4096
-    trans = 2 * vs * 8 + vs * (8 + 4 + 8 * (2 * 30 + 2)) + n * 16 * 4 + (304 * nrhs * 4 + 32 * 16 * nrhs + 16 * nrhs) * 8 \
+    trans = 2 * vs * 8 + vs * (8 + 4 + 8 * (2 * 30 + 2) + 16) + n * 16 * 4 + (304 * nrhs * 4 + 32 * 16 * nrhs + 16 * nrhs) * 8 \
         + 4096 + n * (4 * 1040 + 2048)
     return per + trans
 
