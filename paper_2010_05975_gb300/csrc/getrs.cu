@@ -268,12 +268,14 @@ __device__ __forceinline__ void solve_stage_t(T* dst, int cp, const T* src, size
 }
 
 // out[i][c] (op) = sum_{p < np} C[i][p] * Bm[p][c] for rows i < nr, p in
-// order.  A thread sums a 4 x 4 tile (rows 4 rg.., columns 4 cg..): per four
-// p it reads four 16-byte pieces of C rows and four of Bm rows for 64
-// multiply-adds, the ratio that keeps the shared-memory reads (their bytes
-// into registers, not the multiply-adds, bound these small products) low.
-// C row pitch cp and Bm row pitch NCW give 16-byte aligned rows.  sub: out =
-// base - sum; else out = sum.
+// order.  A thread sums a 4 x 4 tile (rows rg, rg + NB/4, rg + NB/2,
+// rg + 3 NB/4, columns 4 cg..): per four p it reads four 16-byte pieces of C
+// rows and four of Bm rows for 64 multiply-adds, the ratio that keeps the
+// shared-memory reads (their bytes into registers, not the multiply-adds,
+// bound these small products) low; a warp's eight row groups are
+// consecutive rows, whose 16-byte pieces fall in distinct bank groups (row
+// pitch an odd number of 16-byte chunks).  C row pitch cp and Bm row pitch
+// NCW give 16-byte aligned rows.  sub: out = base - sum; else out = sum.
 template <typename T>
 __device__ __forceinline__ void solve_ld4(const T* p, T (&v)[4]) {
     if constexpr (sizeof(T) == 4) {
@@ -300,21 +302,22 @@ __device__ __forceinline__ void solve_rows(const T* C, int cp, const T* Bm, int 
     constexpr int CG = NCW / 4;                        // column groups of four
     constexpr int NT = (NB / RB) * CG;                 // threads in use
     static_assert(NT <= kSolveThreads, "one thread per (row group, column group)");
+    constexpr int RS = NB / RB;                        // row stride: rows rg, rg + RS, ...
     if (threadIdx.x >= NT) return;
     const int cg = threadIdx.x % CG, rg = threadIdx.x / CG;
-    const int i0 = rg * RB, c = 4 * cg;
-    if (i0 >= nr) return;
+    const int c = 4 * cg;
+    if (rg >= nr) return;
     T acc[RB][4];
 #pragma unroll
     for (int r = 0; r < RB; ++r)
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[r][k] = T(0);
-    const T* Cr = C + static_cast<size_t>(i0) * cp;
+    const T* Cr = C + static_cast<size_t>(rg) * cp;
     const int np4 = np & ~3;
     for (int p = 0; p < np4; p += 4) {
         T cv[RB][4];
 #pragma unroll
-        for (int r = 0; r < RB; ++r) solve_ld4(Cr + r * cp + p, cv[r]);
+        for (int r = 0; r < RB; ++r) solve_ld4(Cr + r * RS * cp + p, cv[r]);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             T bv[4];
@@ -331,12 +334,12 @@ __device__ __forceinline__ void solve_rows(const T* C, int cp, const T* Bm, int 
 #pragma unroll
         for (int r = 0; r < RB; ++r)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) acc[r][k] = fma(Cr[r * cp + p], bv[k], acc[r][k]);
+            for (int k = 0; k < 4; ++k) acc[r][k] = fma(Cr[r * RS * cp + p], bv[k], acc[r][k]);
     }
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
-        if (i0 + r >= nr) break;
-        const size_t i = static_cast<size_t>(i0 + r);
+        if (rg + r * RS >= nr) break;
+        const size_t i = static_cast<size_t>(rg + r * RS);
 #pragma unroll
         for (int k = 0; k < 4; ++k) out[i * ostride + c + k] = sub ? base[i * bstride + c + k] - acc[r][k] : acc[r][k];
     }
