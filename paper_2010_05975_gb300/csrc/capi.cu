@@ -24,7 +24,7 @@ static void ws_free(FactorWs& ws, cudaStream_t s) {
 static int ws_alloc(FactorWs& ws, int m, int b, int h, size_t elem, cudaStream_t s) {
     ws.stride_nodes = static_cast<size_t>(cdiv(m, h > 0 ? h : 1)) + 1;
     bool ok = cudaMallocAsync(reinterpret_cast<void**>(&ws.lists), 2 * ws.stride_nodes * b * sizeof(int), s) == cudaSuccess &&
-              cudaMallocAsync(reinterpret_cast<void**>(&ws.counts), 2 * ws.stride_nodes * sizeof(int), s) == cudaSuccess &&
+              cudaMallocAsync(reinterpret_cast<void**>(&ws.counts), 4 * ws.stride_nodes * sizeof(int), s) == cudaSuccess &&
               cudaMallocAsync(&ws.a00, static_cast<size_t>(b) * b * elem, s) == cudaSuccess &&
               cudaMallocAsync(reinterpret_cast<void**>(&ws.mv), (1 + 4 * static_cast<size_t>(b)) * sizeof(int), s) == cudaSuccess;
     if (!ok) {

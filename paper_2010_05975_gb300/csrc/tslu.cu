@@ -125,14 +125,25 @@ __device__ __forceinline__ void warp_argmax(T& v, int& p, int& l) {
 template <typename T>
 constexpr int tslu_threads() { return sizeof(T) == 4 ? 512 : kTsluThreads; }
 
-// MODE 1: one-CTA nodes, blocked GEPP; MODE 2: nodes over a cluster,
+// What changes from one tree level to the next (the rest is in LevelArgs).
+struct LevelView {
+    int level, nchild, root;
+    const int* child_list;
+    const int* child_cnt;
+    int* out_list;
+    int* out_cnt;
+};
+
+// One node of one tree level (the CTA, or cluster of a.C CTAs, that runs
+// it).  MODE 1: one-CTA nodes, blocked GEPP; MODE 2: nodes over a cluster,
 // cluster-blocked GEPP; MODE 0: nodes over a cluster, column-by-column GEPP.
-// Separate instantiations, so that each keeps its own register allocation.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs<T> a) {
+// Child lists and counts are read through L2 (in the one-launch tree they
+// were written by other CTAs of the same launch).  Ends with a block (or
+// cluster) barrier.
+template <typename T, int MODE, bool LA_ONLY = false>
+__device__ __forceinline__ void tslu_node(const LevelArgs<T>& a, const LevelView& v, int node) {
     cg::cluster_group cluster = cg::this_cluster();
     const int q = static_cast<int>(cluster.block_rank());
-    const int node = blockIdx.x / a.C;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarp = blockDim.x >> 5;
     const int w = a.w, ws = a.ws;
@@ -140,27 +151,27 @@ __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs
     int nr, r0 = 0, cl = 0;
     const int* lp = nullptr;
     const int* rp = nullptr;
-    if (a.level == 0) {
+    if (v.level == 0) {
         r0 = a.k + node * a.H;
         nr = min(a.H, a.m - r0);
     } else {
         const int left = 2 * node, right = 2 * node + 1;
-        cl = a.child_cnt[left];
-        lp = a.child_list + static_cast<size_t>(left) * w;
-        if (right >= a.nchild) {            // odd last node goes up unchanged
+        cl = __ldcg(v.child_cnt + left);
+        lp = v.child_list + static_cast<size_t>(left) * w;
+        if (right >= v.nchild) {            // odd last node goes up unchanged
             if (q == 0) {
-                for (int i = tid; i < cl; i += blockDim.x) a.out_list[static_cast<size_t>(node) * w + i] = lp[i];
-                if (tid == 0) a.out_cnt[node] = cl;
+                for (int i = tid; i < cl; i += blockDim.x) v.out_list[static_cast<size_t>(node) * w + i] = __ldcg(lp + i);
+                if (tid == 0) v.out_cnt[node] = cl;
             }
             return;
         }
-        rp = a.child_list + static_cast<size_t>(right) * w;
-        nr = cl + a.child_cnt[right];
+        rp = v.child_list + static_cast<size_t>(right) * w;
+        nr = cl + __ldcg(v.child_cnt + right);
     }
-    if (!(a.root || nr > w)) {              // a node that keeps all its rows
+    if (!(v.root || nr > w)) {              // a node that keeps all its rows
         if (q == 0) {
-            for (int i = tid; i < nr; i += blockDim.x) a.out_list[static_cast<size_t>(node) * w + i] = r0 + i;
-            if (tid == 0) a.out_cnt[node] = nr;
+            for (int i = tid; i < nr; i += blockDim.x) v.out_list[static_cast<size_t>(node) * w + i] = r0 + i;
+            if (tid == 0) v.out_cnt[node] = nr;
         }
         return;
     }
@@ -181,12 +192,12 @@ __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs
 
     const int i0 = q * a.R;
     const int nloc = max(0, min(a.R, nr - i0));
-    if (MODE != 0 && a.level > 0) {
+    if (MODE != 0 && v.level > 0) {
         // The blocked GEPPs break ties by row: stack the candidates in
         // ascending position order (the selection does not depend on it);
         // this CTA keeps ranks [i0, i0 + nloc).
         int* tmp = reinterpret_cast<int*>(W);             // nr positions, before the rows arrive
-        for (int i = tid; i < nr; i += blockDim.x) tmp[i] = (i < cl) ? lp[i] : rp[i - cl];
+        for (int i = tid; i < nr; i += blockDim.x) tmp[i] = (i < cl) ? __ldcg(lp + i) : __ldcg(rp + i - cl);
         __syncthreads();
         for (int i = tid; i < nr; i += blockDim.x) {
             const int pi = tmp[i];
@@ -198,7 +209,7 @@ __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs
     }
     for (int r = warp; r < nloc; r += nwarp) {
         const int gi = i0 + r;
-        const int pos = (a.level == 0) ? (r0 + gi) : (MODE != 0) ? ids[r] : (gi < cl ? lp[gi] : rp[gi - cl]);
+        const int pos = (v.level == 0) ? (r0 + gi) : (MODE != 0) ? ids[r] : (gi < cl ? __ldcg(lp + gi) : __ldcg(rp + gi - cl));
         if (lane == 0) {
             ids[r] = pos;
             ord[r] = -1;
@@ -212,7 +223,7 @@ __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs
     const int ns = min(nr, w);
     if constexpr (MODE == 1) {
         __shared__ GeppSlots<T> gslots;
-        if (sizeof(T) == 4 && blockDim.x >= 512 && nloc <= 256) {
+        if (LA_ONLY || (sizeof(T) == 4 && blockDim.x >= 512 && nloc <= 256)) {
             // binary32 nodes: the update warps run one panel behind the row warps
             __shared__ unsigned s_zmp[2];
             node_gepp_la<T>(W, ws, nloc, w, ns, ids, ord, winp, lrow, gslots, s_zmp, &s_zero);
@@ -222,7 +233,7 @@ __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs
     } else if constexpr (MODE == 2) {
         __shared__ GeppClusterSlot<T> cslot;
         node_gepp_cluster<T>(W, ws, nloc, a.R, a.C, q, w, ns, ids, ord, winp, Ub, cslot, q == 0 ? &s_zero : nullptr,
-                             a.root != 0);
+                             v.root != 0);
     } else {
         // Row groups: tpr (a power of two <= 32) threads per row, all in one warp.
         int tpr = 1;
@@ -365,10 +376,10 @@ __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs
     __syncthreads();
 
     if (q == 0) {
-        for (int i = tid; i < ns; i += blockDim.x) a.out_list[static_cast<size_t>(node) * w + i] = winp[i];
-        if (tid == 0) a.out_cnt[node] = ns;
+        for (int i = tid; i < ns; i += blockDim.x) v.out_list[static_cast<size_t>(node) * w + i] = winp[i];
+        if (tid == 0) v.out_cnt[node] = ns;
     }
-    if (a.root) {
+    if (v.root) {
         for (int r = warp; r < nloc; r += nwarp) {
             const int o = ord[r];
             if (o < 0) continue;
@@ -377,6 +388,50 @@ __global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(LevelArgs
         if (q == 0 && tid == 0 && s_zero >= 0 && *a.info == 0) *a.info = a.k + s_zero + 1;
     }
     cluster.sync();     // no CTA leaves while another may still read its shared memory
+}
+
+// One tree level per launch: node = blockIdx.x / a.C.  Separate
+// instantiations per mode, so that each keeps its own register allocation.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(tslu_threads<T>()) tslu_level_kernel(const __grid_constant__ LevelArgs<T> a) {
+    const LevelView v{a.level, a.nchild, a.root, a.child_list, a.child_cnt, a.out_list, a.out_cnt};
+    tslu_node<T, MODE>(a, v, static_cast<int>(blockIdx.x) / a.C);
+}
+
+// The whole tree in one launch, for one-CTA nodes (MODE 1; binary32 nodes
+// of at most 256 rows, which take the lookahead GEPP): CTA i runs leaf
+// i, then climbs.  A node's two children end on different CTAs; the one
+// that finishes second (an atomic count per parent node, `arrive`, zero at
+// launch) goes on with the parent, the other exits, so no CTA ever waits
+// for another.  A node without a sibling (the odd last one) passes its list
+// up by itself.  Level L's nodes sit at list/count index base_L + node
+// (base_0 = 0, base_{L+1} = base_L + nodes_L).  a describes level 0.
+template <typename T>
+__global__ void __launch_bounds__(tslu_threads<T>()) tslu_tree_kernel(const __grid_constant__ LevelArgs<T> a0,
+                                                                      int* __restrict__ arrive) {
+    __shared__ int s_go;
+    int node = static_cast<int>(blockIdx.x), nn = a0.nnode, base = 0, pbase = 0, pnn = 0;
+    for (int level = 0;; ++level) {
+        const LevelView v{level, pnn, nn == 1 ? 1 : 0, a0.out_list + static_cast<size_t>(pbase) * a0.w,
+                          a0.out_cnt + pbase, a0.out_list + static_cast<size_t>(base) * a0.w, a0.out_cnt + base};
+        tslu_node<T, 1, sizeof(T) == 4>(a0, v, node);
+        if (nn == 1) return;
+        __threadfence();                                  // this node's list (and a00) before the count
+        __syncthreads();
+        if ((node ^ 1) < nn) {
+            if (threadIdx.x == 0) {
+                s_go = atomicAdd(arrive + base + nn + (node >> 1), 1);
+                __threadfence();                          // the sibling's list after the count
+            }
+            __syncthreads();
+            if (s_go == 0) return;                        // the sibling is still running: it goes on
+        }
+        pbase = base;
+        pnn = nn;
+        base += nn;
+        nn = (nn + 1) >> 1;
+        node >>= 1;
+    }
 }
 
 template <typename T>
@@ -476,6 +531,30 @@ int tslu_select(const T* A, int lda, int m, int k, int w, int h, int* lists, int
     args.root = (nn == 1);
     args.child_list = nullptr;
     args.child_cnt = nullptr;
+    // (binary32 nodes must fit the lookahead GEPP: rows <= 256 on 512 threads)
+    if (sh.blocked == 1 && sh.C == 1 && (sizeof(T) == 8 || (sh.R <= 256 && tslu_threads<T>() >= 512))) {
+        // the whole tree in one launch: lists and counts level after level,
+        // arrival counts after the counts (2 list_stride_nodes each)
+        args.out_list = lists;
+        args.out_cnt = counts;
+        int* arrive = counts + 2 * list_stride_nodes;
+        int total = 0, rbase = 0;
+        for (int k = nn; ; k = (k + 1) >> 1) {
+            rbase = total;
+            total += k;
+            if (k == 1) break;
+        }
+        LU_TRY(cudaMemsetAsync(arrive, 0, sizeof(int) * static_cast<size_t>(total), s));
+        {
+            ProfScope ps(LU_PROF_TSLU, s);
+            if (int rc_ = smem_attr(tslu_tree_kernel<T>, sh.smem)) return rc_;
+            tslu_tree_kernel<T><<<nn, tslu_threads<T>(), sh.smem, s>>>(args, arrive);
+            count_launches(1);
+        }
+        LU_LAUNCHED();
+        *root_list = lists + static_cast<size_t>(rbase) * w;
+        return 0;
+    }
     args.out_list = list_buf[cur];
     args.out_cnt = cnt_buf[cur];
     if (int rc = launch_level(args, nn, sh.C, sh.smem, s)) return rc;
