@@ -17,8 +17,10 @@
  * Ownership.  Matrix, vector, pivot and info pointers are DEVICE pointers
  * owned by the caller, unless an argument says "host".  The library keeps no
  * pointer past the work it enqueues on the given stream.  Internal workspace
- * is taken from the stream-ordered allocator (cudaMallocAsync) and returned
- * on the same stream.
+ * is taken stream-ordered (cudaMallocFromPoolAsync) from a memory pool the
+ * library creates per device and returned on the same stream; the pool
+ * keeps up to 16 GB of freed memory reserved for the next calls, and the
+ * caller's default pool is not touched.
  *
  * Asynchrony.  Every call validates its arguments on the host, enqueues its
  * work on `stream` and returns; results are ready when the stream reaches
@@ -105,6 +107,15 @@ int lu_factor(int n, double *A, int lda, int *piv, int *info, cudaStream_t strea
  */
 int lu_factor_ex(int m, int n, double *A, int lda, int *piv, int *info,
                  const lu_opts *opts, cudaStream_t stream);
+
+/*
+ * lu_memory_pool -- the memory pool (a cudaMemPool_t) from which the library
+ * takes its stream-ordered workspace on the current device, created on first
+ * use with a release threshold of 16 GB: for inspection
+ * (cudaMemPoolGetAttribute) or trimming (cudaMemPoolTrimTo) by the caller.
+ * Returns -1 for a null pointer, LU_ELAUNCH if the pool cannot be created.
+ */
+int lu_memory_pool(void **pool);
 
 /*
  * lu_factor_host -- lu_factor_ex on a matrix in HOST memory: the call copies

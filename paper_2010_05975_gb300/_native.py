@@ -112,6 +112,7 @@ _SIGS = {
     "chol_solve": ([I, I, P, I, P, I, P], I),
     "chol_solve_f32": ([I, I, P, I, P, I, P], I),
     "lu_residual": ([I, I, P, I, P, I, P, I, P, I, P, P], I),
+    "lu_memory_pool": ([ctypes.POINTER(ctypes.c_void_p)], I),
     "ir_solve": ([I, I, P, I, P, I, P, I, ctypes.POINTER(ir_opts), ctypes.POINTER(ir_result), P], I),
     "lu_factor_batched": ([I, P, P, P, P, P, I, P], I),
     "lu_solve_batched": ([I, P, P, P, P, P, P, P, I, P], I),

@@ -462,7 +462,7 @@ static int factor_batched(int batch, const int* n, T* const* A, const int* lda, 
                           const bat::Widths& widths, cudaStream_t s) {
     int* ws = nullptr;
     const size_t words = static_cast<size_t>(batch) + (bat::kMaxN + 2) + 4;
-    if (cudaMallocAsync(reinterpret_cast<void**>(&ws), words * sizeof(int), s) != cudaSuccess) {
+    if (lu_malloc_async(reinterpret_cast<void**>(&ws), words * sizeof(int), s) != cudaSuccess) {
         cudaGetLastError();
         return LU_ENOMEM;
     }

@@ -5,6 +5,41 @@
 
 namespace lu {
 
+// The library's memory pools, one per device (see lu_malloc_async).
+static cudaError_t lib_pool(cudaMemPool_t* out) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    if (cudaError_t e = cudaGetDevice(&dev)) return e;
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = pools.find(dev);
+        if (it != pools.end()) {
+            pool = it->second;
+        } else {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            if (cudaError_t e = cudaMemPoolCreate(&pool, &props)) return e;
+            unsigned long long keep = 16ull << 30;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            pools[dev] = pool;
+        }
+    }
+    *out = pool;
+    return cudaSuccess;
+}
+
+cudaError_t lu_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool = nullptr;
+    if (cudaError_t e = lib_pool(&pool)) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+
 struct FactorWs {
     int* lists = nullptr;
     int* counts = nullptr;
@@ -23,10 +58,10 @@ static void ws_free(FactorWs& ws, cudaStream_t s) {
 
 static int ws_alloc(FactorWs& ws, int m, int b, int h, size_t elem, cudaStream_t s) {
     ws.stride_nodes = static_cast<size_t>(cdiv(m, h > 0 ? h : 1)) + 1;
-    bool ok = cudaMallocAsync(reinterpret_cast<void**>(&ws.lists), 2 * ws.stride_nodes * b * sizeof(int), s) == cudaSuccess &&
-              cudaMallocAsync(reinterpret_cast<void**>(&ws.counts), 4 * ws.stride_nodes * sizeof(int), s) == cudaSuccess &&
-              cudaMallocAsync(&ws.a00, static_cast<size_t>(b) * b * elem, s) == cudaSuccess &&
-              cudaMallocAsync(reinterpret_cast<void**>(&ws.mv), (1 + 4 * static_cast<size_t>(b)) * sizeof(int), s) == cudaSuccess;
+    bool ok = lu_malloc_async(reinterpret_cast<void**>(&ws.lists), 2 * ws.stride_nodes * b * sizeof(int), s) == cudaSuccess &&
+              lu_malloc_async(reinterpret_cast<void**>(&ws.counts), 4 * ws.stride_nodes * sizeof(int), s) == cudaSuccess &&
+              lu_malloc_async(&ws.a00, static_cast<size_t>(b) * b * elem, s) == cudaSuccess &&
+              lu_malloc_async(reinterpret_cast<void**>(&ws.mv), (1 + 4 * static_cast<size_t>(b)) * sizeof(int), s) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         ws_free(ws, s);
@@ -192,10 +227,10 @@ static int factor_lowp(int m, int n, float* A, int lda, int* piv, int* info, int
     const size_t nblk = static_cast<size_t>(cdiv(n, 256)) + 1;
     bool ok = true;
     for (int i = 0; i < d && ok; ++i)
-        ok = cudaMallocAsync(reinterpret_cast<void**>(&slot[i].Lq), static_cast<size_t>(m) * kLowpK * elem + 256, s) == cudaSuccess &&
-             cudaMallocAsync(reinterpret_cast<void**>(&slot[i].Uq), static_cast<size_t>(n) * kLowpK * elem + 256, s) == cudaSuccess &&
-             cudaMallocAsync(reinterpret_cast<void**>(&slot[i].eLrow), (static_cast<size_t>(m) + 1) * sizeof(int), s) == cudaSuccess &&
-             cudaMallocAsync(reinterpret_cast<void**>(&slot[i].eU), nblk * sizeof(int), s) == cudaSuccess;
+        ok = lu_malloc_async(reinterpret_cast<void**>(&slot[i].Lq), static_cast<size_t>(m) * kLowpK * elem + 256, s) == cudaSuccess &&
+             lu_malloc_async(reinterpret_cast<void**>(&slot[i].Uq), static_cast<size_t>(n) * kLowpK * elem + 256, s) == cudaSuccess &&
+             lu_malloc_async(reinterpret_cast<void**>(&slot[i].eLrow), (static_cast<size_t>(m) + 1) * sizeof(int), s) == cudaSuccess &&
+             lu_malloc_async(reinterpret_cast<void**>(&slot[i].eU), nblk * sizeof(int), s) == cudaSuccess;
     FactorWs ws;
     int rc = ok ? ws_alloc(ws, m, b, h, sizeof(float), s) : LU_ENOMEM;
     float* a00 = static_cast<float*>(ws.a00);
@@ -292,10 +327,10 @@ extern "C" int lu_gemm_lowp(int M, int N, int K, const float* L, int ldl, const 
     const size_t elem = fp8 ? 1 : 2;
     unsigned char *Lq = nullptr, *Uq = nullptr;
     int *eL = nullptr, *eU = nullptr;
-    bool ok = cudaMallocAsync(reinterpret_cast<void**>(&Lq), static_cast<size_t>(M) * kLowpK * elem + 256, stream) == cudaSuccess &&
-              cudaMallocAsync(reinterpret_cast<void**>(&Uq), static_cast<size_t>(N) * kLowpK * elem + 256, stream) == cudaSuccess &&
-              cudaMallocAsync(reinterpret_cast<void**>(&eL), (static_cast<size_t>(M) + 1) * sizeof(int), stream) == cudaSuccess &&
-              cudaMallocAsync(reinterpret_cast<void**>(&eU), (static_cast<size_t>(cdiv(N, 256)) + 1) * sizeof(int), stream) == cudaSuccess;
+    bool ok = lu_malloc_async(reinterpret_cast<void**>(&Lq), static_cast<size_t>(M) * kLowpK * elem + 256, stream) == cudaSuccess &&
+              lu_malloc_async(reinterpret_cast<void**>(&Uq), static_cast<size_t>(N) * kLowpK * elem + 256, stream) == cudaSuccess &&
+              lu_malloc_async(reinterpret_cast<void**>(&eL), (static_cast<size_t>(M) + 1) * sizeof(int), stream) == cudaSuccess &&
+              lu_malloc_async(reinterpret_cast<void**>(&eU), (static_cast<size_t>(cdiv(N, 256)) + 1) * sizeof(int), stream) == cudaSuccess;
     int rc = LU_ENOMEM;
     if (ok) {
         // The quantizers read the operands as blocks of one matrix: L as
@@ -323,6 +358,17 @@ extern "C" int lu_factor_ex(int m, int n, double* A, int lda, int* piv, int* inf
     return factor_loop<double>(m, n, A, lda, piv, info, b, h, SchurF64{}, stream);
 }
 
+extern "C" int lu_memory_pool(void** pool) {
+    if (pool == nullptr) return -1;
+    cudaMemPool_t p = nullptr;
+    if (lib_pool(&p) != cudaSuccess) {
+        cudaGetLastError();
+        return LU_ELAUNCH;
+    }
+    *pool = static_cast<void*>(p);
+    return 0;
+}
+
 extern "C" int lu_factor_host(int m, int n, double* A, int lda, int* piv, int* info, const lu_opts* opts,
                               cudaStream_t stream) {
     int b, h, prec;
@@ -334,8 +380,8 @@ extern "C" int lu_factor_host(int m, int n, double* A, int lda, int* piv, int* i
     const size_t row = static_cast<size_t>(n) * sizeof(double);
     double* dA = nullptr;
     int* dpiv = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void**>(&dA), row * m, stream) != cudaSuccess ||
-        cudaMallocAsync(reinterpret_cast<void**>(&dpiv), (static_cast<size_t>(kmax) + 1) * sizeof(int), stream) !=
+    if (lu_malloc_async(reinterpret_cast<void**>(&dA), row * m, stream) != cudaSuccess ||
+        lu_malloc_async(reinterpret_cast<void**>(&dpiv), (static_cast<size_t>(kmax) + 1) * sizeof(int), stream) !=
             cudaSuccess) {
         cudaGetLastError();
         if (dA) cudaFreeAsync(dA, stream);

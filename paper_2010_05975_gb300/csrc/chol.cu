@@ -83,7 +83,7 @@ static int chol_loop(int n, T* A, int lda, int* info, int b, cudaStream_t s) {
     LU_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
     if (n == 0) return 0;
     T* Ut = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void**>(&Ut), static_cast<size_t>(b) * b * sizeof(T), s) != cudaSuccess) {
+    if (lu_malloc_async(reinterpret_cast<void**>(&Ut), static_cast<size_t>(b) * b * sizeof(T), s) != cudaSuccess) {
         cudaGetLastError();
         return LU_ENOMEM;
     }

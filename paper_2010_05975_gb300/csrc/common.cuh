@@ -25,6 +25,13 @@
 
 namespace lu {
 
+// Stream-ordered device allocation from the library's own memory pool (one
+// per device, created on first use): freed memory stays reserved for reuse
+// up to 16 GB instead of going back to the driver at every synchronize, so
+// repeated calls do not re-map their workspace; the caller's default pool
+// is left alone.  Same contract as cudaMallocAsync; free with cudaFreeAsync.
+cudaError_t lu_malloc_async(void** p, size_t bytes, cudaStream_t s);
+
 // 16-byte asynchronous copy global -> shared (cp.async); bytes < 16 reads
 // that many and zero-fills the rest (0: nothing is read).  Both addresses
 // 16-byte aligned.  cp_async_wait_all() waits for the thread's own copies.

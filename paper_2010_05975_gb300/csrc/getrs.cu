@@ -725,13 +725,13 @@ int solve_plan_make(int n, const T* LU, int lda, const int* piv, SolvePlan<T>* p
     p->chol = piv == nullptr ? 1 : 0;
     if (n == 0) return 0;
     const int nblk = cdiv(n, NB);
-    if (cudaMallocAsync(reinterpret_cast<void**>(&p->perm), sizeof(int) * static_cast<size_t>(n), s) != cudaSuccess ||
-        cudaMallocAsync(reinterpret_cast<void**>(&p->DT), sizeof(T) * static_cast<size_t>(nblk) * 2 * NB * NB, s) !=
+    if (lu_malloc_async(reinterpret_cast<void**>(&p->perm), sizeof(int) * static_cast<size_t>(n), s) != cudaSuccess ||
+        lu_malloc_async(reinterpret_cast<void**>(&p->DT), sizeof(T) * static_cast<size_t>(nblk) * 2 * NB * NB, s) !=
             cudaSuccess ||
         (sizeof(T) == 4 &&
-         cudaMallocAsync(reinterpret_cast<void**>(&p->M), sizeof(T) * static_cast<size_t>(nblk) * 2 * NB * NB, s) !=
+         lu_malloc_async(reinterpret_cast<void**>(&p->M), sizeof(T) * static_cast<size_t>(nblk) * 2 * NB * NB, s) !=
              cudaSuccess) ||
-        cudaMallocAsync(reinterpret_cast<void**>(&p->off), sizeof(int) * (2 * static_cast<size_t>(nblk) + 1), s) !=
+        lu_malloc_async(reinterpret_cast<void**>(&p->off), sizeof(int) * (2 * static_cast<size_t>(nblk) + 1), s) !=
             cudaSuccess) {
         cudaGetLastError();
         solve_plan_free(p, s);
@@ -806,7 +806,7 @@ int solve_plan_apply(const SolvePlan<T>& p, int nrhs, T* B, int ldb, cudaStream_
     const size_t flags = sizeof(SolveSync) + sizeof(int) * (2 * static_cast<size_t>(nflag) + 2 * nblk);
     const size_t fbytes = (flags + 255) / 256 * 256;
     void* ws = nullptr;
-    if (cudaMallocAsync(&ws, fbytes + sizeof(T) * 2 * vs, s) != cudaSuccess) {
+    if (lu_malloc_async(&ws, fbytes + sizeof(T) * 2 * vs, s) != cudaSuccess) {
         cudaGetLastError();
         return LU_ENOMEM;
     }

@@ -460,7 +460,7 @@ extern "C" int lu_residual(int n, int nrhs, const double* A, int lda, const doub
     if (n == 0 || nrhs == 0) return 0;
     double* ws = nullptr;
     const size_t words = static_cast<size_t>(kRedBlocks) * nrhs + 4 * static_cast<size_t>(nrhs) + kRedBlocks + 8;
-    if (cudaMallocAsync(reinterpret_cast<void**>(&ws), words * sizeof(double), stream) != cudaSuccess) {
+    if (lu_malloc_async(reinterpret_cast<void**>(&ws), words * sizeof(double), stream) != cudaSuccess) {
         cudaGetLastError();
         return LU_ENOMEM;
     }
@@ -505,7 +505,7 @@ struct Dev {
     template <typename T>
     T* alloc(size_t count) {
         void* p = nullptr;
-        if (cudaMallocAsync(&p, count * sizeof(T) + 16, s) != cudaSuccess) {
+        if (lu_malloc_async(&p, count * sizeof(T) + 16, s) != cudaSuccess) {
             cudaGetLastError();
             ok = false;
             return nullptr;
@@ -744,11 +744,11 @@ namespace lu {
 // Factor a binary32 copy of A at `prec` (LU_PREC_FP8 / BF16 / F32).
 int ir_factor(int n, const double* A, int lda, int prec, int b, int h, IrFactors* f, cudaStream_t s) {
     if (f->A32 == nullptr) {
-        if (cudaMallocAsync(reinterpret_cast<void**>(&f->A32), static_cast<size_t>(n) * n * sizeof(float) + 16, s) !=
+        if (lu_malloc_async(reinterpret_cast<void**>(&f->A32), static_cast<size_t>(n) * n * sizeof(float) + 16, s) !=
                 cudaSuccess ||
-            cudaMallocAsync(reinterpret_cast<void**>(&f->piv), static_cast<size_t>(n) * sizeof(int) + 16, s) !=
+            lu_malloc_async(reinterpret_cast<void**>(&f->piv), static_cast<size_t>(n) * sizeof(int) + 16, s) !=
                 cudaSuccess ||
-            cudaMallocAsync(reinterpret_cast<void**>(&f->info), 2 * sizeof(int), s) != cudaSuccess) {
+            lu_malloc_async(reinterpret_cast<void**>(&f->info), 2 * sizeof(int), s) != cudaSuccess) {
             cudaGetLastError();
             return LU_ENOMEM;
         }
@@ -992,7 +992,7 @@ extern "C" int ir_solve(int n, int nrhs, const double* A, int lda, const double*
 // its memory up front so that no request can fail halfway on an allocation,
 // or a process whose GPU memory is owned by another framework's caching
 // allocator.  Its reduction scratch is a fixed array in this file instead of
-// a cudaMallocAsync buffer, which bounds nrhs.
+// a pool buffer, which bounds nrhs.
 // ---------------------------------------------------------------------------
 namespace lu {
 

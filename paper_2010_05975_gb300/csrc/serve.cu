@@ -448,7 +448,7 @@ void Server::run_batch(std::vector<Req*>& rs, cudaStream_t s) {
                 v.Ause = r->bA;
                 v.ldu = r->blda;
             } else {
-                good = cudaMallocAsync(reinterpret_cast<void**>(&v.A64), nn * sizeof(double), s) == cudaSuccess &&
+                good = lu_malloc_async(reinterpret_cast<void**>(&v.A64), nn * sizeof(double), s) == cudaSuccess &&
                        (r->borrow ? cudaMemcpy2DAsync(v.A64, sizeof(double) * n, r->bA, sizeof(double) * r->blda,
                                                       sizeof(double) * n, n, kin, s)
                                   : cudaMemcpyAsync(v.A64, r->A.data(), nn * sizeof(double), cudaMemcpyHostToDevice,
@@ -456,15 +456,15 @@ void Server::run_batch(std::vector<Req*>& rs, cudaStream_t s) {
                 v.Ause = v.A64;
                 v.ldu = n;
             }
-            good = good && cudaMallocAsync(reinterpret_cast<void**>(&v.F), nn * sizeof(float), s) == cudaSuccess &&
-                   cudaMallocAsync(reinterpret_cast<void**>(&v.piv), (static_cast<size_t>(n) + 1) * sizeof(int), s) ==
+            good = good && lu_malloc_async(reinterpret_cast<void**>(&v.F), nn * sizeof(float), s) == cudaSuccess &&
+                   lu_malloc_async(reinterpret_cast<void**>(&v.piv), (static_cast<size_t>(n) + 1) * sizeof(int), s) ==
                        cudaSuccess;
         }
-        good = good && cudaMallocAsync(reinterpret_cast<void**>(&v.B64), vs * sizeof(double), s) == cudaSuccess &&
-               cudaMallocAsync(reinterpret_cast<void**>(&v.X64), vs * sizeof(double), s) == cudaSuccess &&
-               cudaMallocAsync(reinterpret_cast<void**>(&v.R64), vs * sizeof(double), s) == cudaSuccess &&
-               cudaMallocAsync(reinterpret_cast<void**>(&v.r32), vs * sizeof(float), s) == cudaSuccess &&
-               cudaMallocAsync(reinterpret_cast<void**>(&v.cw), 2 * static_cast<size_t>(nr) * sizeof(double), s) ==
+        good = good && lu_malloc_async(reinterpret_cast<void**>(&v.B64), vs * sizeof(double), s) == cudaSuccess &&
+               lu_malloc_async(reinterpret_cast<void**>(&v.X64), vs * sizeof(double), s) == cudaSuccess &&
+               lu_malloc_async(reinterpret_cast<void**>(&v.R64), vs * sizeof(double), s) == cudaSuccess &&
+               lu_malloc_async(reinterpret_cast<void**>(&v.r32), vs * sizeof(float), s) == cudaSuccess &&
+               lu_malloc_async(reinterpret_cast<void**>(&v.cw), 2 * static_cast<size_t>(nr) * sizeof(double), s) ==
                    cudaSuccess;
         good = good && (r->borrow ? cudaMemcpy2DAsync(v.B64, sizeof(double) * nr, r->bB, sizeof(double) * r->bldb,
                                                       sizeof(double) * nr, n, kin, s)
@@ -551,7 +551,7 @@ void Server::run_batch(std::vector<Req*>& rs, cudaStream_t s) {
             if (keep && v.A64 == nullptr) {
                 // a borrowed device matrix: the cache keeps its own copy
                 const size_t nn = static_cast<size_t>(r->n) * r->n;
-                if (cudaMallocAsync(reinterpret_cast<void**>(&v.A64), nn * sizeof(double), s) != cudaSuccess ||
+                if (lu_malloc_async(reinterpret_cast<void**>(&v.A64), nn * sizeof(double), s) != cudaSuccess ||
                     cudaMemcpy2DAsync(v.A64, sizeof(double) * r->n, v.Ause, sizeof(double) * v.ldu,
                                       sizeof(double) * r->n, r->n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
                     cudaGetLastError();
@@ -666,7 +666,7 @@ void Server::run(Req* r, cudaStream_t s) {
             Ause = r->bA;                                     // the caller's device matrix, read in place
             ldu = r->blda;
         } else {
-            if (cudaMallocAsync(reinterpret_cast<void**>(&A64), nn * sizeof(double), s) != cudaSuccess) rc = LU_ENOMEM;
+            if (lu_malloc_async(reinterpret_cast<void**>(&A64), nn * sizeof(double), s) != cudaSuccess) rc = LU_ENOMEM;
             if (!rc) {
                 const cudaError_t e =
                     r->borrow ? cudaMemcpy2DAsync(A64, sizeof(double) * n, r->bA, sizeof(double) * r->blda,
@@ -677,8 +677,8 @@ void Server::run(Req* r, cudaStream_t s) {
             Ause = A64;
         }
     }
-    if (!rc && (cudaMallocAsync(reinterpret_cast<void**>(&B64), sizeof(double) * n * nr, s) != cudaSuccess ||
-                cudaMallocAsync(reinterpret_cast<void**>(&X64), sizeof(double) * n * nr, s) != cudaSuccess))
+    if (!rc && (lu_malloc_async(reinterpret_cast<void**>(&B64), sizeof(double) * n * nr, s) != cudaSuccess ||
+                lu_malloc_async(reinterpret_cast<void**>(&X64), sizeof(double) * n * nr, s) != cudaSuccess))
         rc = LU_ENOMEM;
     if (!rc) {
         const cudaError_t e =
@@ -714,7 +714,7 @@ void Server::run(Req* r, cudaStream_t s) {
     bool keep = ok && r->matrix_id != 0 && cache_.find(r->matrix_id) == cache_.end();
     if (keep && A64 == nullptr) {
         // a borrowed device matrix: the cache keeps its own copy
-        if (cudaMallocAsync(reinterpret_cast<void**>(&A64), nn * sizeof(double), s) != cudaSuccess ||
+        if (lu_malloc_async(reinterpret_cast<void**>(&A64), nn * sizeof(double), s) != cudaSuccess ||
             cudaMemcpy2DAsync(A64, sizeof(double) * n, Ause, sizeof(double) * ldu, sizeof(double) * n, n,
                               cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
             cudaGetLastError();

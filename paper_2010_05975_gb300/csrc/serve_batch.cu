@@ -255,7 +255,7 @@ int batch_solve(std::vector<BatchReq>& h, const std::vector<double>& tol, int ma
     const size_t bytes = sizeof(BatchReq) * nb + sizeof(int) * nb + sizeof(double) * nb +
                          (sizeof(void*) * 2 + sizeof(int) * 3) * static_cast<size_t>(nf > 0 ? nf : 1) + 256;
     unsigned char* ws = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void**>(&ws), bytes, s) != cudaSuccess) {
+    if (lu_malloc_async(reinterpret_cast<void**>(&ws), bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return LU_ENOMEM;
     }

@@ -36,16 +36,21 @@ def _entry():
     return L
 
 
-class DefaultPool:
-    """Read-only view of the current device's default stream-ordered memory
-    pool through the driver API (the pool cudaMallocAsync draws from)."""
+class Pool:
+    """Read-only view of a stream-ordered memory pool through the driver API:
+    the current device's default pool (what cudaMallocAsync draws from), or
+    the library's own pool (lu_memory_pool, where its workspace comes from)."""
 
-    def __init__(self, torch):
+    def __init__(self, torch, library=None):
         self.cu = ctypes.CDLL("libcuda.so.1")
-        dev = ctypes.c_int(0)
-        assert self.cu.cuDeviceGet(ctypes.byref(dev), torch.cuda.current_device()) == 0
         self.pool = ctypes.c_void_p(0)
-        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+        if library is None:
+            dev = ctypes.c_int(0)
+            assert self.cu.cuDeviceGet(ctypes.byref(dev), torch.cuda.current_device()) == 0
+            assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+        else:
+            library.lu_memory_pool.argtypes = [ctypes.POINTER(ctypes.c_void_p)]
+            assert library.lu_memory_pool(ctypes.byref(self.pool)) == 0
 
     def get(self, attr):
         v = ctypes.c_uint64(0)
@@ -95,12 +100,14 @@ def test_noalloc_matches_host_residual_and_oracle_twice(oracle_mod):
 
 def test_noalloc_allocates_nothing():
     """Around a call (after a first one, which may load the library's device
-    code), the default pool's used-memory high watermark stays where it was
-    and the device's free memory does not change; the same measurement around
-    lu_residual does see its workspace allocation."""
+    code), the used-memory high watermarks of the default pool and of the
+    library's pool stay where they were and the device's free memory does not
+    change; the same measurement around lu_residual does see its workspace
+    allocation in the library's pool."""
     torch = cuda_or_fail()
     L = _entry()
-    pool = DefaultPool(torch)
+    dpool = Pool(torch)
+    pool = Pool(torch, L)
     n, nr = 1000, 12
     A = torch.from_numpy(wl.matrix_uniform(n, n, seed=7)).cuda()
     X = torch.from_numpy(wl.matrix_normal(n, nr, seed=8)).cuda()
@@ -110,21 +117,22 @@ def test_noalloc_allocates_nothing():
     eta = torch.empty(nr, dtype=torch.float64, device="cuda")
     s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
-    def measured(fn):
+    def measured(fn, p):
         torch.cuda.synchronize()
-        pool.reset_high()
-        used0 = pool.get(_USED_MEM_CURRENT)
+        p.reset_high()
+        used0 = p.get(_USED_MEM_CURRENT)
         free0 = torch.cuda.mem_get_info()[0]
         for _ in range(2):
             assert fn(n, nr, A.data_ptr(), n, X.data_ptr(), nr, B.data_ptr(), nr, R.data_ptr(), nr,
                       eta.data_ptr(), s) == 0
         torch.cuda.synchronize()
-        return used0, pool.get(_USED_MEM_HIGH), free0, torch.cuda.mem_get_info()[0]
+        return used0, p.get(_USED_MEM_HIGH), free0, torch.cuda.mem_get_info()[0]
 
-    used0, high, free0, free1 = measured(L.lu_residual_noalloc)
-    assert high == used0
-    assert free1 == free0
-    used0, high, _, _ = measured(L.lu_residual)
+    for p in (dpool, pool):
+        used0, high, free0, free1 = measured(L.lu_residual_noalloc, p)
+        assert high == used0
+        assert free1 == free0
+    used0, high, _, _ = measured(L.lu_residual, pool)
     assert high > used0                      # the check sees a stream-ordered allocation
 
 
