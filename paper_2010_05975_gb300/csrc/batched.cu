@@ -279,12 +279,8 @@ __device__ void schur(Smem<T>& sm, T* A, int lda, int n, int k, int w) {
         }
         for (int tc = 0; tc < tiles; ++tc) {
             const int j0 = r0 + tc * kTile;
-            __syncthreads();
-            for (int e = tid; e < w * kTile; e += blockDim.x) {
-                const int p = e / kTile, j = e % kTile;
-                Us[p * kTile + j] = (j0 + j < n) ? A[idx(k + p, j0 + j, lda)] : T(0);
-            }
-            __syncthreads();
+            // the tile's current values first: their loads fly while U12's
+            // columns are staged
             T acc[4][4];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
@@ -293,6 +289,12 @@ __device__ void schur(Smem<T>& sm, T* A, int lda, int n, int k, int w) {
                     const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
                     acc[a][b] = (i < n && j < n) ? A[idx(i, j, lda)] : T(0);
                 }
+            __syncthreads();
+            for (int e = tid; e < w * kTile; e += blockDim.x) {
+                const int p = e / kTile, j = e % kTile;
+                Us[p * kTile + j] = (j0 + j < n) ? A[idx(k + p, j0 + j, lda)] : T(0);
+            }
+            __syncthreads();
             for (int p = 0; p < w; ++p) {
                 T lv[4], uv[4];
 #pragma unroll
