@@ -356,8 +356,9 @@ typedef struct {
  * first use binary32 multiplies (A and z rounded to binary32, 32-term
  * binary32 runs summed in binary64) with an inner tolerance of 1e-6: the
  * outer binary64 residual corrects what they miss.  Once such a cycle cuts
- * eta by less than 10x (kappa too large for them) the products are
- * binary64.  When a binary64 FGMRES cycle
+ * eta by less than 10x the products are binary64 (kappa too large for
+ * them), unless the factors are fp8: those are refactored in bf16 first and
+ * the binary32 products kept.  When a binary64 FGMRES cycle
  * gains less than 10x, or two cycles do not reach tol, the matrix is
  * refactored one precision up (fp8 -> bf16 -> fp32) and refinement goes on
  * from the current X.  max_iter bounds the refinement steps over all levels.

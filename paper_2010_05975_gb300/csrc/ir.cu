@@ -18,7 +18,9 @@
 // correction equation only has to be solved to a relative accuracy well
 // above binary32's, since the next binary64 residual measures and corrects
 // what the cycle missed; a cycle that cuts eta by less than 10x shows the
-// products too coarse for this matrix, and later cycles use binary64 ones.
+// products too coarse for this matrix, and later cycles use binary64 ones --
+// except with fp8 factors, whose poor preconditioning is the likelier cause:
+// those are refactored in bf16 and keep the binary32 products.
 //
 // Multi-column blocks are n x nrhs row-major.  Reductions are two-pass with
 // fixed order, so results do not depend on scheduling.
@@ -881,9 +883,15 @@ int ir_refine(IrFactors* fac, const double* A, int lda, int nrhs, const double* 
                 return 0;
             }
             if (total_it >= max_iter) return 0;
-            // a binary32-product cycle that gained less than 10x: binary64
-            // products from now on; that cycle does not count below
+            // a binary32-product cycle that gained less than 10x: with fp8
+            // factors the preconditioner is what failed, so refactor in bf16
+            // and keep the binary32 products; otherwise binary64 products from
+            // now on.  Either way that cycle does not count below.
             if (last_mv32 && opt.krylov_products == 0 && em > 0.1 * prev) {
+                if (fac->precision == LU_PREC_FP8) {
+                    escalate = true;
+                    break;
+                }
                 mv32 = false;
                 cycles = 0;
             }
