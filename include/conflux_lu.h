@@ -125,7 +125,9 @@ int lu_memory_pool(void **pool);
  *   m, n, lda, opts  as lu_factor_ex (opts->precision must be 0 or F64)
  *   A     HOST, m x n row-major; overwritten by L and U.  Page-locked memory
  *         (cudaHostAlloc / cudaHostRegister) lets the copies run at the
- *         link's rate; pageable memory works, more slowly.
+ *         link's rate, and each step's b finished rows then go back while
+ *         the later steps run; pageable memory works, more slowly, and gets
+ *         all of L\U back after the last step.
  *   piv   HOST int[min(m, n)]
  *   info  HOST int
  * Device memory: one m x n binary64 buffer plus the factorization's

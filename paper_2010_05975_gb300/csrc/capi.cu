@@ -96,9 +96,16 @@ struct SchurF32 {
 // The next tournament reads only those panel columns, so it runs on a
 // high-priority side stream concurrently with the rest of the update; the
 // next step's pivot application waits for both.
-template <typename T, typename Schur>
+struct NoRowsDone {
+    int operator()(int, int, cudaEvent_t) const { return 0; }
+};
+
+// `done(k, kn, ready)` runs once step k has enqueued all its work: rows
+// [k, kn) are then final in every column once `ready` has fired (later steps
+// swap and update only rows >= kn).
+template <typename T, typename Schur, typename RowsDone = NoRowsDone>
 static int factor_loop(int m, int n, T* A, int lda, int* piv, int* info, int b, int h, const Schur& schur,
-                       cudaStream_t s) {
+                       cudaStream_t s, const RowsDone& done = RowsDone{}) {
     LU_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
     const int kmax = m < n ? m : n;
     if (kmax == 0) return 0;
@@ -149,6 +156,8 @@ static int factor_loop(int m, int n, T* A, int lda, int* piv, int* info, int b, 
         } else {
             rc = schur(A, lda, m, k, w, kn, n, s);
         }
+        // ev_u12 follows this step's row moves (through ev_piv) and its U12
+        if (!rc) rc = done(k, kn, ev_u12);
     }
     // join the side stream before the workspace goes back to the pool
     if (ev_tslu && s2) {
@@ -392,23 +401,61 @@ extern "C" int lu_factor_host(int m, int n, double* A, int lda, int* piv, int* i
     // a contiguous matrix moves as one linear copy each way (a pitched copy
     // of 8.6 GB may be split into row transfers)
     const bool contig = (lda == n);
-    const size_t bytes = row * static_cast<size_t>(m);
-    if ((contig ? cudaMemcpyAsync(dA, A, bytes, cudaMemcpyHostToDevice, stream)
-                : cudaMemcpy2DAsync(dA, row, A, static_cast<size_t>(lda) * sizeof(double), row, m,
-                                    cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+    const size_t hpitch = static_cast<size_t>(lda) * sizeof(double);
+    // rows [r0, r1) of the device copy back to A on stream cs
+    auto rows_back = [&](int r0, int r1, cudaStream_t cs) {
+        if (r1 <= r0) return cudaSuccess;
+        const double* src = dA + static_cast<size_t>(r0) * n;
+        double* dst = A + static_cast<size_t>(r0) * lda;
+        const size_t nr = static_cast<size_t>(r1 - r0);
+        return contig ? cudaMemcpyAsync(dst, src, row * nr, cudaMemcpyDeviceToHost, cs)
+                      : cudaMemcpy2DAsync(dst, hpitch, src, row, row, nr, cudaMemcpyDeviceToHost, cs);
+    };
+    if ((contig ? cudaMemcpyAsync(dA, A, row * static_cast<size_t>(m), cudaMemcpyHostToDevice, stream)
+                : cudaMemcpy2DAsync(dA, row, A, hpitch, row, m, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
         rc = LU_ELAUNCH;
-    if (!rc) rc = factor_loop<double>(m, n, dA, n, dpiv, dinfo, b, h, SchurF64{}, stream);
-    if (!rc && ((contig ? cudaMemcpyAsync(A, dA, bytes, cudaMemcpyDeviceToHost, stream)
-                        : cudaMemcpy2DAsync(A, static_cast<size_t>(lda) * sizeof(double), dA, row, row, m,
-                                            cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+    // With page-locked host memory each step's finished rows go back on a
+    // copy stream while later steps run (a copy into pageable memory would
+    // block this thread until the step finished, so those rows go back at
+    // the end).  The copies then use the link throughout the factorization
+    // instead of as one 8.6 GB transfer after it.
+    cudaPointerAttributes attr{};
+    const bool pinned = cudaPointerGetAttributes(&attr, A) == cudaSuccess && attr.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev_cs = nullptr;
+    if (pinned && (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+                   cudaEventCreateWithFlags(&ev_cs, cudaEventDisableTiming) != cudaSuccess))
+        rc = LU_ELAUNCH;
+    int sent = 0;  // rows [0, sent) are on their way back
+    auto done = [&](int k, int kn, cudaEvent_t ready) {
+        if (!cs) return 0;
+        if (cudaStreamWaitEvent(cs, ready, 0) != cudaSuccess || rows_back(k, kn, cs) != cudaSuccess)
+            return static_cast<int>(LU_ELAUNCH);
+        sent = kn;
+        return 0;
+    };
+    if (!rc) rc = factor_loop<double>(m, n, dA, n, dpiv, dinfo, b, h, SchurF64{}, stream, done);
+    if (!rc && (rows_back(sent, m, stream) != cudaSuccess ||
                 cudaMemcpyAsync(piv, dpiv, static_cast<size_t>(kmax) * sizeof(int), cudaMemcpyDeviceToHost,
                                 stream) != cudaSuccess ||
                 cudaMemcpyAsync(info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess))
         rc = LU_ELAUNCH;
+    // the copy stream reads dA: join it before dA goes back to the pool
+    if (cs) {
+        if (ev_cs) {
+            cudaEventRecord(ev_cs, cs);
+            cudaStreamWaitEvent(stream, ev_cs, 0);
+        } else {
+            cudaStreamSynchronize(cs);
+        }
+    }
     cudaGetLastError();
     cudaFreeAsync(dA, stream);
     cudaFreeAsync(dpiv, stream);
     if (cudaStreamSynchronize(stream) != cudaSuccess && !rc) rc = LU_ELAUNCH;
+    if (ev_cs) cudaEventDestroy(ev_cs);
+    if (cs) cudaStreamDestroy(cs);
     return rc;
 }
 

@@ -117,7 +117,8 @@ def test_ir_solve_passes_the_timeout_up():
 
 
 @pytest.mark.parametrize("pinned", [True, False])
-@pytest.mark.parametrize("m,n,lda,b", [(700, 700, 710, 64), (1500, 1200, 1200, 128), (300, 500, 503, 32)])
+@pytest.mark.parametrize("m,n,lda,b", [(700, 700, 710, 64), (640, 640, 640, 64), (1500, 1200, 1200, 128),
+                                        (300, 500, 503, 32)])
 def test_host_factor_equals_device_factor(m, n, lda, b, pinned):
     """lu_factor_host (host buffers, copies inside the call) returns the
     device factorization's L\\U, pivots and info bit for bit."""
