@@ -9,69 +9,73 @@
 // kernels give each thread one row (column) and sweep it left-looking in
 // register blocks against the triangle staged in shared memory: no barrier
 // between steps.  The binary64 kernels, bound by the DFMA pipe, keep the
-// right-looking sweep with four threads per row (column).
+// right-looking sweep with eight threads per row (column).
 #include "common.cuh"
 #include "prof.cuh"
 
 namespace lu {
 
-constexpr int kL21Rows = 64;      // rows of A21 per CTA
-constexpr int kL21Stride = kL21Rows + 1;
-constexpr int kU12Cols = 64;      // columns of A12 per CTA
+// Rows of A21 (columns of A12) per CTA of 256 threads: 32 in binary64, so
+// that a 256-wide panel's tile (64 KB) lets three CTAs share an SM and the
+// late steps' short blocks still spread over every SM; 64 in binary32.
+template <typename E>
+__host__ __device__ constexpr int trsm_tile_rows() { return sizeof(E) == 8 ? 32 : 64; }
 
-// Tile T[j][r] (column-major over the CTA's rows, padded stride).  Thread t
-// owns row r = t % 64 and columns c = j+1+g, j+1+g+4, ... with g = t / 64.
-// U (w x w, row stride ldu) is read on and above its diagonal only: the LU
-// passes A00 in place, the Cholesky factorization L00^T.
+// Tile T[j][r] (column-major over the CTA's R rows, padded stride R + 1).
+// Thread t owns row r = t % R and columns c = j+1+g, j+1+g+G, ... with
+// g = t / R and G = 256 / R.  U (w x w, row stride ldu) is read on and above
+// its diagonal only: the LU passes A00 in place, the Cholesky factorization
+// L00^T.
 template <typename E>
 __global__ void __launch_bounds__(256) trsm_l21_kernel(E* __restrict__ A, int lda, int m, int k, int w,
                                                        const E* __restrict__ U, int ldu) {
+    constexpr int R = trsm_tile_rows<E>(), G = 256 / R, ST = R + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     E* T = reinterpret_cast<E*>(smem_raw);
-    const int r0 = k + w + blockIdx.x * kL21Rows;
-    const int nrow = min(kL21Rows, m - r0);
+    const int r0 = k + w + blockIdx.x * R;
+    const int nrow = min(R, m - r0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int r = warp; r < kL21Rows; r += nwarp) {
+    for (int r = warp; r < R; r += nwarp) {
         const bool ok = r < nrow;
-        for (int j = lane; j < w; j += 32) T[j * kL21Stride + r] = ok ? A[idx(r0 + r, k + j, lda)] : E(0);
+        for (int j = lane; j < w; j += 32) T[j * ST + r] = ok ? A[idx(r0 + r, k + j, lda)] : E(0);
     }
     __syncthreads();
-    const int r = threadIdx.x % kL21Rows, g = threadIdx.x / kL21Rows;
+    const int r = threadIdx.x % R, g = threadIdx.x / R;
     for (int j = 0; j < w; ++j) {
         const E* Uj = U + idx(j, 0, ldu);
         if (g == 0) {
             const E u = Uj[j];
-            const E a = T[j * kL21Stride + r];
-            T[j * kL21Stride + r] = (u != E(0)) ? a / u : E(0);
+            const E a = T[j * ST + r];
+            T[j * ST + r] = (u != E(0)) ? a / u : E(0);
         }
         __syncthreads();
-        const E x = T[j * kL21Stride + r];
-        for (int c = j + 1 + g; c < w; c += 4) T[c * kL21Stride + r] = fma(-x, Uj[c], T[c * kL21Stride + r]);
+        const E x = T[j * ST + r];
+        for (int c = j + 1 + g; c < w; c += G) T[c * ST + r] = fma(-x, Uj[c], T[c * ST + r]);
         __syncthreads();
     }
     for (int rr = warp; rr < nrow; rr += nwarp)
-        for (int j = lane; j < w; j += 32) A[idx(r0 + rr, k + j, lda)] = T[j * kL21Stride + rr];
+        for (int j = lane; j < w; j += 32) A[idx(r0 + rr, k + j, lda)] = T[j * ST + rr];
 }
 
-// Tile T[i][c] (row-major, w rows x 64 columns).  Thread t owns column
-// c = t % 64 and rows i = p+1+g, p+1+g+4, ... with g = t / 64.
+// Tile T[i][c] (row-major, w rows x C columns, C = trsm_tile_rows).  Thread
+// t owns column c = t % C and rows i = p+1+g, p+1+g+G, ... with g = t / C.
 template <typename E>
 __global__ void __launch_bounds__(256) trsm_u12_kernel(E* __restrict__ A, int lda, int n, int k, int w) {
+    constexpr int C = trsm_tile_rows<E>(), G = 256 / C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     E* T = reinterpret_cast<E*>(smem_raw);
-    const int c0 = k + w + blockIdx.x * kU12Cols;
-    const int ncol = min(kU12Cols, n - c0);
-    const int c = threadIdx.x % kU12Cols, g = threadIdx.x / kU12Cols;
-    for (int i = g; i < w; i += 4) T[i * kU12Cols + c] = (c < ncol) ? A[idx(k + i, c0 + c, lda)] : E(0);
+    const int c0 = k + w + blockIdx.x * C;
+    const int ncol = min(C, n - c0);
+    const int c = threadIdx.x % C, g = threadIdx.x / C;
+    for (int i = g; i < w; i += G) T[i * C + c] = (c < ncol) ? A[idx(k + i, c0 + c, lda)] : E(0);
     __syncthreads();
     for (int p = 0; p + 1 < w; ++p) {
-        const E up = T[p * kU12Cols + c];
-        for (int i = p + 1 + g; i < w; i += 4)
-            T[i * kU12Cols + c] = fma(-A[idx(k + i, k + p, lda)], up, T[i * kU12Cols + c]);
+        const E up = T[p * C + c];
+        for (int i = p + 1 + g; i < w; i += G) T[i * C + c] = fma(-A[idx(k + i, k + p, lda)], up, T[i * C + c]);
         __syncthreads();
     }
     if (c < ncol)
-        for (int i = g; i < w; i += 4) A[idx(k + i, c0 + c, lda)] = T[i * kU12Cols + c];
+        for (int i = g; i < w; i += G) A[idx(k + i, c0 + c, lda)] = T[i * C + c];
 }
 
 // ---------------------------------------------------------------------------
@@ -256,7 +260,7 @@ __global__ void __launch_bounds__(kRowCta) trsm_u12_cols_kernel(float* __restric
 }
 
 // Panels wider than this much shared memory allows (w > 384) take the
-// four-threads-per-row kernels.
+// right-looking kernels above.
 constexpr size_t kTrsmSmemMax = 200 * 1024;
 
 // 16-byte asynchronous staging needs every staged row to start 16-byte
@@ -281,9 +285,10 @@ int trsm_l21(E* A, int lda, int m, int k, int w, const E* U, int ldu, cudaStream
         }
     }
     if (!done) {
-        const size_t smem = static_cast<size_t>(w) * kL21Stride * sizeof(E);
+        constexpr int R = trsm_tile_rows<E>();
+        const size_t smem = static_cast<size_t>(w) * (R + 1) * sizeof(E);
         if (int rc_ = smem_attr(trsm_l21_kernel<E>, smem)) return rc_;
-        trsm_l21_kernel<E><<<cdiv(rows, kL21Rows), 256, smem, s>>>(A, lda, m, k, w, U, ldu);
+        trsm_l21_kernel<E><<<cdiv(rows, R), 256, smem, s>>>(A, lda, m, k, w, U, ldu);
     }
     count_launches(1);
     LU_LAUNCHED();
@@ -306,9 +311,10 @@ int trsm_u12(E* A, int lda, int n, int k, int w, cudaStream_t s) {
         }
     }
     if (!done) {
-        const size_t smem = static_cast<size_t>(w) * kU12Cols * sizeof(E);
+        constexpr int C = trsm_tile_rows<E>();
+        const size_t smem = static_cast<size_t>(w) * C * sizeof(E);
         if (int rc_ = smem_attr(trsm_u12_kernel<E>, smem)) return rc_;
-        trsm_u12_kernel<E><<<cdiv(cols, kU12Cols), 256, smem, s>>>(A, lda, n, k, w);
+        trsm_u12_kernel<E><<<cdiv(cols, C), 256, smem, s>>>(A, lda, n, k, w);
     }
     count_launches(1);
     LU_LAUNCHED();
